@@ -1,0 +1,151 @@
+/*
+ * pbvd.h -- C ABI of the GB300 parallel block-based Viterbi decoder.
+ *
+ * The decoder implements the parallel block-based Viterbi decoding of
+ * Peng, Liu, Hou, Zhao, "A Gb/s Parallel Block-based Viterbi Decoder for
+ * Convolutional Codes on GPU" (arXiv 1608.00066):
+ *   - the stream of n trellis stages is cut into blocks of D stages; block b
+ *     decodes stages [bD, min((b+1)D, n)) (Sec. III-A, Fig. 1);
+ *   - each block runs the forward add-compare-select recursion of Eq. (1)
+ *     from L stages before its first stage ("truncation" stages, starting
+ *     from all-zero metrics, or from the known encoder state S_0 when that
+ *     range reaches stage 0) to L stages after its last stage;
+ *   - it then traces back from state S_0 at its last forward stage, with no
+ *     metric comparison (Sec. III-A, Algorithm 1), and emits its D bits.
+ * Branch metrics are computed once per distinct codeword per stage and reused
+ * by every butterfly of the same group (Sec. III-B, Eqs. (3)-(6)).
+ *
+ * Conventions
+ *   state d = (D_{v-1} ... D_0)_2, v = K - 1; S_{2j}, S_{2j+1} move to S_j
+ *   (input 0) and S_{j + 2^{v-1}} (input 1); decoded bit of a state = D_{v-1}.
+ *   gens[r] holds generator r+1 as an integer whose bit K-1 is the tap on the
+ *   input bit and bit 0 the tap on D_0 (octal 0171 = [1111001], Eq. (2)).
+ *   Soft values are int8, positive favouring code bit 0; -128 is read as -127.
+ *   Branch metric sum_r |lambda_r - mu(c_r)|, mu(0) = +127, mu(1) = -127.
+ *   In Eq. (1) a tie keeps the predecessor S_{2j} (the upper branch).
+ *   The known start gives S_0 metric 0 and every other state 8192.
+ *   Streams and frames are zero-terminated: the last stage is traced back
+ *   from S_0, which is exact when the encoder was flushed with v zero bits.
+ *
+ * Memory: every pointer named d_* is caller-owned device memory; every other
+ * pointer is host memory.  The library never frees caller memory.  A context
+ * owns its constant tables and a device workspace that grows on demand (it
+ * holds the survivor bits of one launch); pbvd_destroy frees them.
+ *
+ * Errors: every call returns PBVD_OK (0) or a negative code; nothing aborts.
+ * Calls are ordered on the CUDA stream passed in (NULL = legacy default
+ * stream); device-side failures surface as PBVD_ECUDA on a later call.
+ * A context is not thread-safe: do not use one context from two host
+ * threads at once, nor in two streams whose work overlaps.
+ */
+#ifndef PBVD_H
+#define PBVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PBVD_API __attribute__((visibility("default")))
+#else
+#define PBVD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pbvd_ctx pbvd_ctx;
+
+enum {
+    PBVD_OK = 0,
+    PBVD_EINVAL = -1,       /* bad argument */
+    PBVD_ENOMEM = -2,       /* device or host allocation failed */
+    PBVD_ECUDA = -3,        /* a CUDA call failed (see pbvd_last_cuda_error) */
+    PBVD_EUNSUPPORTED = -4, /* valid, but no kernel is built for it */
+    PBVD_ETIMEOUT = -5,     /* a bounded device wait ran out */
+    PBVD_EBUSY = -6         /* resource in use (e.g. serving slots full) */
+};
+
+/* Creates a decoder context for an (R,1,K) convolutional code, optionally
+ * punctured, decoded in blocks of D stages with L overlap stages per side.
+ *   K          constraint length, 3 <= K <= 9 (N = 2^{K-1} states)
+ *   R          number of generators (mother rate 1/R), 2 <= R <= 3
+ *   gens       host array of R generator integers (see conventions); each
+ *              must have its input tap (bit K-1) or its oldest tap (bit 0)
+ *              set and no bit at or above K
+ *   puncture   host array R x P, row-major, 0/1: code bit r of stage s is
+ *              sent iff puncture[r*P + s % P]; NULL for no puncturing.
+ *              Every column must send at least one bit.  1 <= P <= 32.
+ *   D          decoded stages per block, a positive multiple of 8
+ *   L          overlap (truncation and traceback) stages, 0 <= L <= 4096
+ * Writes the new context to *out.  Returns PBVD_EINVAL for bad arguments,
+ * PBVD_EUNSUPPORTED when no kernel is built for (K, gens), PBVD_ENOMEM. */
+PBVD_API int pbvd_create(pbvd_ctx **out, int K, int R, const uint32_t *gens,
+                const uint8_t *puncture, int P, int D, int L);
+
+/* Frees the context and its workspace.  Synchronises the device first if
+ * work may still be in flight.  NULL is ignored. */
+PBVD_API void pbvd_destroy(pbvd_ctx *ctx);
+
+/* Decodes one terminated stream or frame of n_stages trellis stages.
+ *   d_llr      device, int8 soft values as sent: n_stages * R values for an
+ *              unpunctured code, otherwise the kept positions only, in stage
+ *              order, code bits of a stage in ascending r
+ *   n_stages   number of trellis stages, tail included (>= 1)
+ *   d_out      device, ceil(n_stages / 8) bytes; bit s of the result is bit
+ *              (s & 7) of byte (s >> 3), LSB first; the last v bits are the tail
+ *   stream     a cudaStream_t (NULL = legacy default stream)
+ * Asynchronous: returns after enqueueing.  Grows the context workspace on
+ * first use of a larger n_stages (a device allocation that synchronises); call
+ * once with the largest size before capturing a CUDA graph. */
+PBVD_API int pbvd_decode(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
+                uint8_t *d_out, void *stream);
+
+/* Number of soft values d_llr must hold for n_stages stages. */
+PBVD_API int pbvd_llr_count(const pbvd_ctx *ctx, size_t n_stages, size_t *count);
+
+/* One frame of a batched decode. */
+typedef struct pbvd_batch_item {
+    pbvd_ctx *ctx;        /* code and (D, L) of this frame */
+    const int8_t *d_llr;  /* device soft values as for pbvd_decode */
+    size_t n_stages;      /* stages of this frame, tail included */
+    uint8_t *d_out;       /* device, ceil(n_stages / 8) bytes */
+} pbvd_batch_item;
+
+/* Decodes n_items independent frames of possibly different codes and lengths
+ * in one persistent kernel launch.  Each frame's result equals pbvd_decode
+ * on that frame alone with the same context.  items is a host array read
+ * during the call; the work list is uploaded into a workspace owned by the
+ * first item's context.  Output ranges must not overlap. */
+PBVD_API int pbvd_decode_batch(const pbvd_batch_item *items, size_t n_items, void *stream);
+
+/* Kernel configuration of a context (the tuning knobs).
+ *   threads_per_pair  T: threads that share one pair of blocks (power of two,
+ *                     N/T states per thread); 0 = automatic
+ *   cta_threads       threads per CTA (multiple of 32, <= 256); 0 = automatic
+ *   survivors_in_smem 1: survivor bits in shared memory, 0: in the device
+ *                     workspace, -1 = automatic */
+typedef struct pbvd_config {
+    int threads_per_pair;
+    int cta_threads;
+    int survivors_in_smem;
+} pbvd_config;
+
+/* Sets the configuration used by later pbvd_decode calls on ctx.
+ * PBVD_EUNSUPPORTED if the code has no kernel for that T. */
+PBVD_API int pbvd_set_config(pbvd_ctx *ctx, const pbvd_config *cfg);
+
+/* Reads back the configuration pbvd_decode would use for n_stages. */
+PBVD_API int pbvd_get_config(const pbvd_ctx *ctx, size_t n_stages, pbvd_config *cfg);
+
+/* Message for an error code (static string). */
+PBVD_API const char *pbvd_strerror(int code);
+
+/* Text of the last CUDA error seen by the library in this process. */
+PBVD_API const char *pbvd_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBVD_H */

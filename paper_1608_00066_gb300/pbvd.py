@@ -1,0 +1,211 @@
+"""Python binding of the C ABI in include/pbvd.h (argument marshalling only).
+
+Every decoding step runs in the CUDA library ``libpbvd.so`` built in-tree by
+``paper_1608_00066_gb300.build``.  There is no CPU fallback: if the library
+cannot be loaded, every call raises ``PbvdError``.
+
+The functions keep the C names: ``pbvd_create``, ``pbvd_decode``,
+``pbvd_decode_batch``, ``pbvd_destroy`` ...  Device buffers are passed as
+integer addresses (e.g. ``tensor.data_ptr()``) and streams as raw
+``cudaStream_t`` handles (e.g. ``torch.cuda.current_stream().cuda_stream``).
+``Decoder`` wraps a context for use with torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpbvd.so")
+
+PBVD_OK = 0
+PBVD_EINVAL = -1
+PBVD_ENOMEM = -2
+PBVD_ECUDA = -3
+PBVD_EUNSUPPORTED = -4
+PBVD_ETIMEOUT = -5
+PBVD_EBUSY = -6
+
+# Exported symbols of include/pbvd.h (checked by the tests).
+EXPORTS = (
+    "pbvd_create", "pbvd_destroy", "pbvd_decode", "pbvd_llr_count", "pbvd_decode_batch",
+    "pbvd_set_config", "pbvd_get_config", "pbvd_strerror", "pbvd_last_cuda_error",
+)
+
+
+class PbvdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = "%s failed: %s (%d)" % (where, _strerror(code), code)
+        if code == PBVD_ECUDA and _lib is not None:
+            msg += " [%s]" % _lib.pbvd_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+class pbvd_config(ctypes.Structure):
+    _fields_ = [("threads_per_pair", ctypes.c_int), ("cta_threads", ctypes.c_int),
+                ("survivors_in_smem", ctypes.c_int)]
+
+
+class pbvd_batch_item(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("d_llr", ctypes.c_void_p),
+                ("n_stages", ctypes.c_size_t), ("d_out", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _strerror(code: int) -> str:
+    if _lib is None:
+        return "error %d" % code
+    return _lib.pbvd_strerror(code).decode()
+
+
+def load(path: Optional[str] = None):
+    """Loads libpbvd.so (raises PbvdError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise PbvdError(PBVD_EUNSUPPORTED, "load %s (run paper_1608_00066_gb300.build)" % p)
+        lib = ctypes.CDLL(p)
+        V, I, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        lib.pbvd_create.argtypes = [ctypes.POINTER(V), I, I, V, V, I, I, I]
+        lib.pbvd_create.restype = I
+        lib.pbvd_destroy.argtypes = [V]
+        lib.pbvd_destroy.restype = None
+        lib.pbvd_decode.argtypes = [V, V, SZ, V, V]
+        lib.pbvd_decode.restype = I
+        lib.pbvd_llr_count.argtypes = [V, SZ, ctypes.POINTER(SZ)]
+        lib.pbvd_llr_count.restype = I
+        lib.pbvd_decode_batch.argtypes = [V, SZ, V]
+        lib.pbvd_decode_batch.restype = I
+        lib.pbvd_set_config.argtypes = [V, ctypes.POINTER(pbvd_config)]
+        lib.pbvd_set_config.restype = I
+        lib.pbvd_get_config.argtypes = [V, SZ, ctypes.POINTER(pbvd_config)]
+        lib.pbvd_get_config.restype = I
+        lib.pbvd_strerror.argtypes = [I]
+        lib.pbvd_strerror.restype = ctypes.c_char_p
+        lib.pbvd_last_cuda_error.argtypes = []
+        lib.pbvd_last_cuda_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str):
+    if rc != PBVD_OK:
+        raise PbvdError(rc, where)
+
+
+# ------------------------------------------------------------ C-named calls
+
+def pbvd_create(K: int, gens: Sequence[int], puncture=None, D: int = 512, L: int = 42) -> int:
+    """Returns a context handle (int).  ``puncture`` is an R x P 0/1 nested
+    sequence or None."""
+    lib = load()
+    R = len(gens)
+    g = (ctypes.c_uint32 * R)(*gens)
+    if puncture is not None:
+        rows = [list(r) for r in puncture]
+        P = len(rows[0])
+        flat = [int(x) for r in rows for x in r]
+        pat = (ctypes.c_uint8 * len(flat))(*flat)
+        pat_p = ctypes.cast(pat, ctypes.c_void_p)
+    else:
+        P, pat_p = 0, None
+    h = ctypes.c_void_p()
+    _check(lib.pbvd_create(ctypes.byref(h), K, R, ctypes.cast(g, ctypes.c_void_p), pat_p, P, D, L),
+           "pbvd_create")
+    return h.value
+
+
+def pbvd_destroy(ctx: int) -> None:
+    load().pbvd_destroy(ctx)
+
+
+def pbvd_decode(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0) -> None:
+    _check(load().pbvd_decode(ctx, d_llr, n_stages, d_out, stream or None), "pbvd_decode")
+
+
+def pbvd_llr_count(ctx: int, n_stages: int) -> int:
+    c = ctypes.c_size_t()
+    _check(load().pbvd_llr_count(ctx, n_stages, ctypes.byref(c)), "pbvd_llr_count")
+    return int(c.value)
+
+
+def pbvd_decode_batch(items: Sequence[tuple], stream: int = 0) -> None:
+    """items: sequence of (ctx, d_llr, n_stages, d_out)."""
+    arr = (pbvd_batch_item * max(len(items), 1))()
+    for i, (ctx, llr, n, out) in enumerate(items):
+        arr[i].ctx, arr[i].d_llr, arr[i].n_stages, arr[i].d_out = ctx, llr, n, out
+    _check(load().pbvd_decode_batch(ctypes.cast(arr, ctypes.c_void_p), len(items), stream or None),
+           "pbvd_decode_batch")
+
+
+def pbvd_set_config(ctx: int, threads_per_pair: int = 0, cta_threads: int = 0,
+                    survivors_in_smem: int = -1) -> None:
+    cfg = pbvd_config(threads_per_pair, cta_threads, survivors_in_smem)
+    _check(load().pbvd_set_config(ctx, ctypes.byref(cfg)), "pbvd_set_config")
+
+
+def pbvd_get_config(ctx: int, n_stages: int) -> dict:
+    cfg = pbvd_config()
+    _check(load().pbvd_get_config(ctx, n_stages, ctypes.byref(cfg)), "pbvd_get_config")
+    return {"threads_per_pair": cfg.threads_per_pair, "cta_threads": cfg.cta_threads,
+            "survivors_in_smem": cfg.survivors_in_smem}
+
+
+def pbvd_strerror(code: int) -> str:
+    return load().pbvd_strerror(code).decode()
+
+
+# ------------------------------------------------------------- convenience
+
+class Decoder:
+    """Owns one context.  ``decode`` takes torch tensors on the GPU."""
+
+    def __init__(self, K: int, gens: Sequence[int], puncture=None, D: int = 512, L: int = 42):
+        self.K, self.gens, self.puncture, self.D, self.L = K, tuple(gens), puncture, D, L
+        self.ctx = pbvd_create(K, gens, puncture, D, L)
+
+    def close(self):
+        if self.ctx:
+            pbvd_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def llr_count(self, n_stages: int) -> int:
+        return pbvd_llr_count(self.ctx, n_stages)
+
+    def set_config(self, **kw):
+        pbvd_set_config(self.ctx, **kw)
+
+    def get_config(self, n_stages: int) -> dict:
+        return pbvd_get_config(self.ctx, n_stages)
+
+    def decode(self, llr, n_stages: int, out=None, stream=None):
+        """llr: int8 CUDA tensor of the sent soft values; returns (or fills) a
+        uint8 CUDA tensor of ceil(n_stages / 8) packed bytes."""
+        import torch
+        if llr.dtype != torch.int8 or not llr.is_cuda or not llr.is_contiguous():
+            raise ValueError("llr must be a contiguous int8 CUDA tensor")
+        if llr.numel() < self.llr_count(n_stages):
+            raise ValueError("llr holds %d values, %d needed" % (llr.numel(), self.llr_count(n_stages)))
+        nbytes = (n_stages + 7) // 8
+        if out is None:
+            out = torch.empty(nbytes, dtype=torch.uint8, device=llr.device)
+        elif out.numel() < nbytes or out.dtype != torch.uint8 or not out.is_cuda:
+            raise ValueError("out must be a uint8 CUDA tensor of %d bytes" % nbytes)
+        s = stream if stream is not None else torch.cuda.current_stream(llr.device)
+        pbvd_decode(self.ctx, llr.data_ptr(), n_stages, out.data_ptr(), s.cuda_stream)
+        return out
