@@ -1,0 +1,329 @@
+"""Benchmark of the parallel block-based Viterbi decoder on GB300.
+
+One step = one pass of the whole hot path over one batch: ingest of the int8
+soft values, branch metrics, add-compare-select, survivor records, traceback
+and packed output, for a terminated stream of 2^24 information bits of the
+K=7 rate-1/2 (171,133) code at Eb/N0 = 3 dB, decoded in blocks of D=512
+stages with L=42 overlap stages (the code, D and L of the paper's
+experiments).  value = decoded information bits / device time, inputs
+resident in HBM; e2e = the same through host buffers (pinned host -> device
+copy, decode, device -> host copy of the decoded bits inside the timed
+region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): blocks are independent, so each rank
+decodes its own stream of the same size (weak scaling, no collective on the
+data path); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+K_INFO = 1 << 24
+EBN0_DB = 3.0
+D_BLOCK, L_OVERLAP = 512, 42
+SEED = 2003
+WORKLOAD = "K7 r1/2 (171,133) terminated stream, 2^24 info bits, BPSK/AWGN Eb/N0 3 dB, int8 soft, D=512 L=42"
+METRIC = "decoded info Gb/s (K=7 r1/2 int8 soft)"
+UNIT = "Gb/s"
+PAPER_CONTEXT = {"GTX980_kernel_Sk_Mbps": 2122.7, "GTX980_3stream_TP_Mbps": 1802.5,
+                 "GTX580_3stream_TP_Mbps": 598.3}
+
+
+def algorithmic_ops_per_bit(N: int, D: int, L: int) -> float:
+    """3N integer operations per stage (two adds and one compare-select per
+    state), times the block overlap (D + 2L) / D, per decoded bit."""
+    return 3.0 * N * (D + 2 * L) / D
+
+
+def peak_int16_ops(sm_count: int = 152, clock_hz: float = 2.07e9) -> float:
+    """Issue-limited integer peak: 4 schedulers x 32 lanes per SM per clock,
+    two 16-bit operations per lane (packed 16x2 arithmetic)."""
+    return sm_count * 4 * 32 * 2 * clock_hz
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._thr:
+            self._thr.join(timeout=6)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 4 + i and s[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def _oracle_worker(args):
+    """Decodes blocks [b0, b1) of the stream with the CPU oracle (child process)."""
+    llr_path, K, gens, n, D, L, b0, b1 = args
+    sys.path.insert(0, ROOT)
+    import oracle as orc
+    llr = np.load(llr_path, mmap_mode="r").reshape(n, 2)
+    t0 = time.perf_counter()
+    orc.viterbi_block(K, gens, llr, D, L, blocks=(b0, b1))
+    dt = time.perf_counter() - t0
+    return 0, dt, int(min(b1 * D, n) - b0 * D)
+
+
+def cpu_oracle_rate(llr: np.ndarray, n: int, target_s: float = 15.0, max_cores=None):
+    """Times the block-based CPU oracle on a bounded sample of the stream's
+    blocks spread over all host cores (spawned processes); returns Mb/s of
+    decoded information bits and a description."""
+    import multiprocessing as mp
+    import tempfile
+    import oracle as orc
+    orc.build()
+    cores = max_cores or os.cpu_count() or 1
+    nb = (n + D_BLOCK - 1) // D_BLOCK
+    tmp = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
+    tmp.close()
+    np.save(tmp.name, llr)
+    gens = (0o171, 0o133)
+    ctx = mp.get_context("spawn")
+    try:
+        with ctx.Pool(cores) as pool:
+            # calibrate: one block per core
+            cal = pool.map(_oracle_worker, [(tmp.name, 7, gens, n, D_BLOCK, L_OVERLAP, 1 + c, 2 + c)
+                                            for c in range(cores)])
+            per_block = max(1e-4, statistics.median(r[1] for r in cal))
+            blocks_per_core = max(1, int(target_s / per_block))
+            blocks_per_core = min(blocks_per_core, max(1, (nb - 2) // cores))
+            jobs = []
+            for c in range(cores):
+                b0 = 1 + c * blocks_per_core
+                jobs.append((tmp.name, 7, gens, n, D_BLOCK, L_OVERLAP, b0, b0 + blocks_per_core))
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, jobs)
+            wall = time.perf_counter() - t0
+    finally:
+        os.unlink(tmp.name)
+    if any(r[0] != 0 for r in res):
+        raise RuntimeError("oracle failed")
+    bits = sum(r[2] for r in res)
+    return {"value": bits / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d blocks (%d info bits), %d spawned processes, %.1f s wall"
+                      % (cores * blocks_per_core, nb, bits, cores, wall)}
+
+
+# -------------------------------------------------------------- our arm
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    from paper_1608_00066_gb300 import build as pbuild
+    from paper_1608_00066_gb300 import pbvd, synth
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    if rank == 0 or world > 1:
+        pbuild.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    spec = synth.K7_R12
+    frame = synth.make_frame(spec, K_INFO, EBN0_DB, seed=SEED + rank)
+    n = frame.n_stages
+    dec = pbvd.Decoder(spec.K, spec.gens, None, D_BLOCK, L_OVERLAP)
+    if args.tune:
+        dec.set_config(**json.loads(args.tune))
+    cfg = dec.get_config(n)
+    d_llr = torch.from_numpy(frame.llr).cuda()
+    nbytes = (n + 7) // 8
+    d_out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (~129 MB)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        dec.decode(d_llr, n, d_out)
+    torch.cuda.synchronize()
+
+    # device-resident: each step decodes the whole stream; L2 is flushed
+    # between steps (outside the timed events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(dev) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            starts[s].record(stream)
+            dec.decode(d_llr, n, d_out, stream=stream)
+            ends[s].record(stream)
+        barrier()
+    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(args.steps)]
+    ms = sum(step_ms) / len(step_ms)
+
+    # correctness of the last output (bit error rate against the message)
+    bits = np.unpackbits(d_out.cpu().numpy(), bitorder="little")[:K_INFO]
+    ber = float((bits != frame.msg).mean())
+
+    # end to end through host buffers
+    h_llr = torch.from_numpy(frame.llr).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        d_llr.copy_(h_llr, non_blocking=True)
+        dec.decode(d_llr, n, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d_llr.copy_(h_llr, non_blocking=True)
+        dec.decode(d_llr, n, d_out, stream=stream)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+
+    value = K_INFO * world / (ms * 1e-3) / 1e9
+    e2e = K_INFO * world / (e2e_ms * 1e-3) / 1e9
+    ops = algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP) * K_INFO
+    peak = peak_int16_ops()
+    achieved = ops / (ms * 1e-3)
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int16x2 (int8 soft input, 16-bit packed path metrics)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "info_bits_per_gpu": K_INFO, "stages": n, "D": D_BLOCK,
+                   "L": L_OVERLAP, "blocks": (n + D_BLOCK - 1) // D_BLOCK, "kernel_config": cfg,
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": "blocks"},
+        "roofline": {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(peak / 1e12, 3),
+                     "unit": "Tops/s (int16)", "frac": round(achieved / peak, 4),
+                     "ops_per_bit": round(algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP), 2),
+                     "traffic": args.traffic},
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(frame.llr.nbytes),
+                "d2h_bytes_per_step": int(nbytes)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "ber": ber,
+        "paper_context": PAPER_CONTEXT,
+    }
+    return result, frame
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tune", default="", help="JSON kernel config (threads_per_pair, cta_threads, ...)")
+    ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    result, frame = run_ours(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_oracle_rate(frame.llr, frame.n_stages)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank: int, world: int):
+    """The reference arm: the CPU oracle (the method as the paper states it,
+    plain C) on the host cores, same workload, metric and unit; each step is a
+    bounded sample of the workload's blocks.  Only rank 0 runs."""
+    if rank != 0:
+        return
+    from paper_1608_00066_gb300 import synth
+    frame = synth.make_frame(synth.K7_R12, K_INFO, EBN0_DB, seed=SEED)
+    vals = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(frame.llr, frame.n_stages, target_s=3.0)
+        if s >= args.warmup:
+            vals.append(r["value"])
+            cb = r
+    v = statistics.mean(vals)
+    cb["value"] = round(v, 6)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "D": D_BLOCK, "L": L_OVERLAP},
+           "cpu_baseline": cb,
+           "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

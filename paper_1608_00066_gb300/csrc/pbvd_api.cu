@@ -53,11 +53,11 @@ Registry& registry() {
 }
 std::mutex g_reg_mu;
 
-int find_entry(int K, int R, const uint32_t* gens, int T) {
+int find_entry(int K, int R, const uint32_t* gens, int T, bool punct) {
   Registry& reg = registry();
   for (size_t i = 0; i < reg.entries.size(); ++i) {
     const KernelEntry& e = reg.entries[i];
-    if (e.K != K || e.R != R || e.T != T) continue;
+    if (e.K != K || e.R != R || e.T != T || e.punct != punct) continue;
     bool same = true;
     for (int r = 0; r < R; ++r) same = same && (e.gens[r] == gens[r]);
     if (same) return (int)i;
@@ -65,9 +65,9 @@ int find_entry(int K, int R, const uint32_t* gens, int T) {
   return -1;
 }
 
-int code_has_any_kernel(int K, int R, const uint32_t* gens) {
+int code_has_any_kernel(int K, int R, const uint32_t* gens, bool punct) {
   for (int T = 1; T <= 32; T *= 2)
-    if (find_entry(K, R, gens, T) >= 0) return 1;
+    if (find_entry(K, R, gens, T, punct) >= 0) return 1;
   return 0;
 }
 
@@ -82,6 +82,7 @@ struct pbvd_ctx {
   int punct_C;           // values sent per period
   uint8_t pattern[3 * 32];
   int16_t punct_off[32 * 4];
+  int16_t punct_pre[33];
   int D, L;
   pbvd_config cfg;
   int device;
@@ -122,11 +123,11 @@ int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p) {
     while (T < want && T < 32) T *= 2;
     T = std::max(T, tmin);
     T = std::min(T, std::min(32, c->N / 2));
-    while (T > tmin && find_entry(c->K, c->R, c->gens, T) < 0) T /= 2;
-    while (T < 32 && find_entry(c->K, c->R, c->gens, T) < 0) T *= 2;
+    while (T > tmin && find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) T /= 2;
+    while (T < 32 && find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) T *= 2;
   }
   p->T = T;
-  p->entry = find_entry(c->K, c->R, c->gens, T);
+  p->entry = find_entry(c->K, c->R, c->gens, T, c->P != 0);
   if (p->entry < 0) return PBVD_EUNSUPPORTED;
   const KernelEntry& e = reg.entries[p->entry];
   const int64_t jmax = (int64_t)c->D + c->L;
@@ -218,7 +219,7 @@ int pbvd_create(pbvd_ctx** out, int K, int R, const uint32_t* gens, const uint8_
       if (!sent) return PBVD_EINVAL;
     }
   }
-  if (!code_has_any_kernel(K, R, gens)) return PBVD_EUNSUPPORTED;
+  if (!code_has_any_kernel(K, R, gens, puncture != nullptr)) return PBVD_EUNSUPPORTED;
 
   pbvd_ctx* c = new (std::nothrow) pbvd_ctx();
   if (!c) return PBVD_ENOMEM;
@@ -232,11 +233,14 @@ int pbvd_create(pbvd_ctx** out, int K, int R, const uint32_t* gens, const uint8_
   c->punct_C = 0;
   if (puncture) {
     int off = 0;
-    for (int col = 0; col < P; ++col)
+    for (int col = 0; col < P; ++col) {
+      c->punct_pre[col] = (int16_t)off;
       for (int r = 0; r < R; ++r) {
         c->pattern[r * 32 + col] = puncture[r * P + col];
         if (puncture[r * P + col]) c->punct_off[col * 4 + r] = (int16_t)off++;
       }
+    }
+    c->punct_pre[P] = (int16_t)off;
     c->punct_C = off;
   }
   c->D = D;
@@ -283,7 +287,7 @@ int pbvd_set_config(pbvd_ctx* c, const pbvd_config* cfg) {
   if (cfg->threads_per_pair != 0) {
     int T = cfg->threads_per_pair;
     if (T < 1 || T > 32 || (T & (T - 1))) return PBVD_EINVAL;
-    if (find_entry(c->K, c->R, c->gens, T) < 0) return PBVD_EUNSUPPORTED;
+    if (find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) return PBVD_EUNSUPPORTED;
   }
   if (cfg->cta_threads != 0 && (cfg->cta_threads < 1 || cfg->cta_threads > 256)) return PBVD_EINVAL;
   if (cfg->survivors_in_smem < -1 || cfg->survivors_in_smem > 1) return PBVD_EINVAL;
@@ -330,6 +334,11 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   a.punct_P = c->P;
   a.punct_C = c->punct_C;
   std::memcpy(a.punct_off, c->punct_off, sizeof(a.punct_off));
+  std::memcpy(a.punct_pre, c->punct_pre, sizeof(a.punct_pre));
+  size_t cnt = 0;
+  pbvd_llr_count(c, n_stages, &cnt);
+  a.llr_count = (int64_t)cnt;
+  a.one = 1u;
   const int64_t grid = ceil_div(p.n_pairs, p.groups);
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];

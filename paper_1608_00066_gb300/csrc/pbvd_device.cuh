@@ -23,12 +23,15 @@
 // memory restores psi = u.  With T = 1 the period is v stages and needs no
 // transpose.
 //
-// Metrics are unsigned 16-bit lanes, renormalised every few stages to
-// PM - PM(S_0) + 14336.  The spread of the metrics of one PB never exceeds
-// 8192 + v * 254 * R <= 14288 (known start) so after renormalisation they lie
-// in [48, 28624] and grow by at most 254 R per stage; with at most 32 stages
-// between renormalisations every candidate stays below 65536 and every
-// difference of two candidates below 32768, so the 16-bit arithmetic is exact.
+// Metrics are 16-bit lanes kept in [0, 32767], renormalised every few
+// stages to PM - PM(S_0) + v * 254 * R.  PM(S_0) is never more than v * 254 * R
+// above the smallest metric and never more than 8192 + v * 254 * R below the
+// largest (8192 = known-start offset), so after renormalisation every metric
+// lies in [0, 2 v 254 R + 8192] (14288 for K=7 R=2, 20384 for K=9 R=3) and
+// grows by at most 254 R per stage; renormalising at least every
+// (32767 - 254 R - 2 v 254 R - 8192) / (254 R) stages keeps every candidate
+// below 32768 and every difference of two candidates below 32768, so the
+// 16-bit (signed-safe) arithmetic is exact.
 //
 // Decision bit of output register k: t = Y - X + (0x8000 + BM(gamma) -
 // BM(alpha)) per lane, i.e. 0x8000 + (c1 - c0); bit 15 of each lane is set
@@ -45,10 +48,8 @@
 namespace pbvd {
 
 constexpr uint32_t kSignBias = 0x80008000u;  // 0x8000 in both 16-bit lanes
-constexpr uint32_t kRenormBase = 0x38003800u; // 14336 in both lanes
 constexpr uint32_t kBigPM = 8192u;            // known-start metric of S_d, d != 0
 constexpr uint32_t kLamMax2 = 0x00FE00FEu;    // 254 in both lanes
-constexpr int kRenormStages = 32;              // max stages between renormalisations
 constexpr int kRing = 16;                      // traceback prefetch: stages per chunk
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
@@ -97,97 +98,222 @@ __host__ __device__ constexpr uint32_t rotl_v(uint32_t x, int s) {
 template <class C, int T>
 struct Shape {
   static constexpr int t = ilog2(T);
-  static constexpr int r = C::v - t;        // register-index bits
-  static constexpr int M = 1 << r;          // states per thread
-  static constexpr int P = (T == 1) ? C::v : r;  // stages per period
-  static constexpr int B = M < 16 ? M : 16;  // registers per survivor word
-  static constexpr int LB = ilog2(B);
-  static constexpr int W = M / B;            // survivor words per thread per stage
-  static constexpr int RENORM_PERIODS = (kRenormStages / P) > 0 ? (kRenormStages / P) : 1;
+  static constexpr int r = C::v - t;               // register-index bits
+  static constexpr int M = 1 << r;                 // states per thread
+  static constexpr int P = (T == 1) ? C::v : r;    // stages per period
+  static constexpr int NB = M / 2;                 // butterflies per thread per stage
+  static constexpr int BPW = NB < 8 ? NB : 8;      // butterflies per survivor word
+  static constexpr int LBPW = ilog2(BPW);
+  static constexpr int W = NB / BPW;               // survivor words per thread per stage
+  static constexpr int RW = T * W;                 // survivor words per stage of a pair
+  static constexpr int CH = P * ((32 + P - 1) / P);  // stages per staged soft-value chunk
+  static constexpr int BMMAX = 254 * C::R;          // largest branch metric
+  static constexpr uint32_t RENORM_BASE = (uint32_t)(C::v * BMMAX) * 0x00010001u;
+  static constexpr int RENORM_STAGES = (32767 - BMMAX - 2 * C::v * BMMAX - (int)kBigPM) / BMMAX;
+  static constexpr int RENORM_PERIODS = RENORM_STAGES / P;
+  static_assert(RENORM_PERIODS >= 1, "renormalisation interval shorter than a period");
   static_assert(r >= 1, "at least two states per thread");
   static_assert(T <= 32, "a group lives in one warp");
 };
 
-// Shared-memory words per group for the transpose / traceback ring, and for
-// survivor records in shared-memory mode.
+// Per-group shared memory (words).  Forward pass: transpose buffer and two
+// raw chunks of soft values per PB.  Traceback (aliases the forward region):
+// per-lane rings of survivor records.  The group stride is padded to T
+// (mod 32) words so the transpose stores of the groups of a warp fall in
+// distinct banks.
+template <class C>
+__host__ __device__ constexpr int raw_chunk_bytes(int CH) {
+  return ((CH * C::R + 15) / 16 + 1) * 16;
+}
+// Transposes write each thread's registers contiguously (stride M + 4 words)
+// and read them back with 16-byte loads when a thread receives at least four
+// consecutive registers from each writer (M / T >= 4); otherwise scalar
+// stores in natural state order and vector reads.
+template <class C, int T>
+__host__ __device__ constexpr bool vector_transpose() {
+  return T > 1 && (Shape<C, T>::M / T) >= 4;
+}
+template <class C, int T>
+__host__ __device__ constexpr int transpose_words() {
+  return (T > 1) ? ((C::N + 4 * T + 3) & ~3) : 0;
+}
+template <class C, int T>
+__host__ __device__ constexpr int raw_offset_words() { return transpose_words<C, T>(); }
+// traceback ring per lane: NBUF chunks of KR records of RW words
+template <class C, int T>
+__host__ __device__ constexpr int tb_kr() {
+  return T <= 2 ? ((32 / Shape<C, T>::RW) > 1 ? (32 / Shape<C, T>::RW) : 1)
+                : ((16 / Shape<C, T>::RW) > 1 ? (16 / Shape<C, T>::RW) : 1);
+}
+template <class C, int T>
+__host__ __device__ constexpr int tb_nbuf() { return T <= 2 ? 4 : 3; }
 template <class C, int T>
 __host__ __device__ constexpr int scratch_words_per_group() {
   using S = Shape<C, T>;
-  int tr = (T > 1) ? (C::N + 4) : 0;
-  int ring = 2 * kRing * T * S::W;
-  int m = tr > ring ? tr : ring;
-  return (m + 3) & ~3;
+  const int fwd = raw_offset_words<C, T>() + (2 * 2 * raw_chunk_bytes<C>(S::CH)) / 4;
+  const int ring = T * tb_nbuf<C, T>() * tb_kr<C, T>() * S::RW;
+  int m = fwd > ring ? fwd : ring;
+  m = (m + 3) & ~3;
+  // group stride that keeps the transposes of the groups of a warp in
+  // distinct banks
+  const int want = vector_transpose<C, T>() ? (T == 2 ? 8 : (T == 4 ? 16 : 4)) : ((T < 4 ? 4 : T) & 31);
+  while ((m & 31) != want) m += 4;
+  return m;
 }
 template <class C, int T>
 __host__ __device__ constexpr int record_words_per_stage() {
-  return T * Shape<C, T>::W;
+  return Shape<C, T>::RW;
 }
 
 // ------------------------------------------------------------- soft input --
 
-// Reads the soft values of one PB stage by stage, inserting erasures (0) at
-// punctured positions.  Only stages inside [f0, f1] are read.
-struct LlrReader {
-  int64_t pos;   // unpunctured: index of the stage's first value
-  int col;       // punctured: column s mod P
-  int64_t base;  // punctured: index of the first value of the period
+// One PB of the pair: where its soft values and output bits live and where
+// it sits in the lock-step stage index i (i = L is stage bD for every PB).
+struct PbRun {
+  const int8_t* src;  // soft value with index vidx(f0)
+  uint8_t* dst;       // output byte holding stage o0
+  int delta;          // lock-step index of stage f0
+  int iend;           // lock-step index of stage f1 (-1: no such PB)
+  int len;            // f1 - f0 + 1
+  int nout;           // o1 - o0
+  int f0mod;          // f0 mod P (punctured)
+  int known_start;    // f0 == 0: start from the known encoder state S_0
+  int rel;            // reader: value index of the next stage, relative to vidx(f0)
+  int col;            // reader: column of the next stage (punctured)
 };
 
+// Geometry of PB b (Sec. III-A): decodes [bD, min((b+1)D, n)) from the
+// forward range [max(0, bD - L), min(n, (b+1)D + L) - 1].
 template <int R>
-__device__ __forceinline__ void llr_init(LlrReader& rd, const KArgs& a, int64_t f0) {
+__device__ __forceinline__ PbRun pb_run(const KArgs& a, const int8_t* llr, uint8_t* out, int64_t n,
+                                        int64_t b) {
+  const int D = a.D, L = a.L;
+  const int64_t s = b * D - L, e = (b + 1) * D + L;
+  const int64_t f0 = s < 0 ? 0 : s;
+  const int64_t f1 = (e < n ? e : n) - 1;
+  const int64_t o0 = b * D;
+  const int64_t o1 = (b + 1) * D < n ? (b + 1) * D : n;
+  PbRun r;
+  r.delta = (int)(L - (o0 - f0));
+  r.len = (int)(f1 - f0 + 1);
+  r.iend = r.delta + r.len - 1;
+  r.nout = (int)(o1 - o0);
+  r.known_start = (f0 == 0);
+  r.dst = out + (o0 >> 3);
+  int64_t v0;
   if (a.punct_P == 0) {
-    rd.pos = f0 * R;
-    rd.col = 0;
-    rd.base = 0;
+    r.f0mod = 0;
+    v0 = f0 * R;
   } else {
-    int64_t per = f0 / a.punct_P;
-    rd.col = (int)(f0 - per * a.punct_P);
-    rd.base = per * a.punct_C;
-    rd.pos = 0;
+    const int64_t per = f0 / a.punct_P;
+    r.f0mod = (int)(f0 - per * a.punct_P);
+    v0 = per * a.punct_C + a.punct_pre[r.f0mod];
+  }
+  r.src = llr + v0;
+  r.rel = 0;
+  r.col = r.f0mod;
+  return r;
+}
+
+// Value index of the first value of stage f0 + k relative to that of f0.
+template <int R>
+__device__ __forceinline__ int rel_value_index(const KArgs& a, int f0mod, int k) {
+  if (a.punct_P == 0) return k * R;
+  const int x = f0mod + k;
+  const int per = x / a.punct_P;
+  return per * a.punct_C + a.punct_pre[x - per * a.punct_P] - a.punct_pre[f0mod];
+}
+
+// Issues the cp.async copies of chunk c (lock-step stages [c*CH, (c+1)*CH))
+// of one PB's soft values into 'buf'; lanes lane, lane + nlanes, ... split
+// the 16-byte pieces.  Pieces that would reach outside the caller's buffer
+// [llr, llr_end) are copied byte by byte with plain loads.  Returns the
+// relative value index held by buf[0].
+template <int R, int CH>
+__device__ __forceinline__ int stage_raw_chunk(const KArgs& a, const PbRun& g, const int8_t* llr,
+                                               const int8_t* llr_end, int c, int8_t* buf, int lane,
+                                               int nlanes) {
+  const int k_lo = max(0, c * CH - g.delta);
+  const int k_hi = min(g.len - 1, c * CH + CH - 1 - g.delta);
+  if (g.iend < 0 || k_lo > k_hi) return 0;
+  const int v0 = rel_value_index<R>(a, g.f0mod, k_lo);
+  const int v1 = rel_value_index<R>(a, g.f0mod, k_hi + 1);
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(llr), hi = reinterpret_cast<uintptr_t>(llr_end);
+  const uintptr_t first = reinterpret_cast<uintptr_t>(g.src) + (uintptr_t)v0;
+  const uintptr_t A0 = first & ~(uintptr_t)15;
+  const uintptr_t A1 = reinterpret_cast<uintptr_t>(g.src) + (uintptr_t)v1;
+  const int npieces = (int)((A1 - A0 + 15) >> 4);
+  for (int p = lane; p < npieces; p += nlanes) {
+    const uintptr_t src = A0 + ((uintptr_t)p << 4);
+    int8_t* dst = buf + (p << 4);
+    if (src >= lo && src + 16 <= hi) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+    } else {
+      for (int q = 0; q < 16; ++q)
+        if (src + q >= lo && src + q < hi) dst[q] = *reinterpret_cast<const int8_t*>(src + q);
+    }
+  }
+  return v0 - (int)(first & 15);
+}
+
+// Raw bytes (zero-extended) of the R code bits of the reader's next stage
+// from the staged chunk 'buf' (whose byte 0 holds relative value index
+// cbase); punctured positions read as 0, the byte of soft value 0.  Advances
+// the reader.
+template <int R, bool PUNCT>
+__device__ __forceinline__ void read_raw(const KArgs& a, PbRun& g, const int8_t* buf, int cbase, uint32_t (&u)[3]) {
+  const uint8_t* p = reinterpret_cast<const uint8_t*>(buf) + (g.rel - cbase);
+  if constexpr (!PUNCT) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) u[q] = p[q];
+    g.rel += R;
+  } else {
+    int used = 0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int off = a.punct_off[g.col * 4 + q];
+      u[q] = off >= 0 ? (uint32_t)p[used] : 0u;
+      used += off >= 0;
+    }
+    g.rel += used;
+    if (++g.col == a.punct_P) g.col = 0;
   }
 }
 
-// Returns the R values of the current stage (clamped to >= -127 and offset
-// by 127, i.e. in [0, 254]) and advances.
-template <int R>
-__device__ __forceinline__ void llr_next(LlrReader& rd, const KArgs& a, const int8_t* __restrict__ llr,
-                                         int (&p)[3]) {
-  if (a.punct_P == 0) {
-#pragma unroll
-    for (int q = 0; q < R; ++q) p[q] = max((int)__ldg(llr + rd.pos + q) + 127, 0);
-    rd.pos += R;
-  } else {
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      int off = a.punct_off[rd.col * 4 + q];
-      p[q] = off >= 0 ? max((int)__ldg(llr + rd.base + off) + 127, 0) : 127;
-    }
-    if (++rd.col == a.punct_P) {
-      rd.col = 0;
-      rd.base += a.punct_C;
-    }
-  }
+// Packs the raw bytes of PB A (low lane) and PB B (high lane) into
+// 127 + max(lambda, -127) per lane: byte ^ 0x80 = lambda + 128, clamped to at
+// least 1, minus 1.
+__device__ __forceinline__ uint32_t pack_soft(uint32_t ua, uint32_t ub) {
+  uint32_t x;
+  asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(x) : "r"(ua), "r"(ub));
+  x = __vmaxu2(x ^ 0x00800080u, 0x00010001u);
+  return x - 0x00010001u;
 }
 
 // ------------------------------------------------------------ ACS stage --
 
 // Branch metrics of all 2^R codewords for both PBs of the pair, and the
-// decision constants kt[c] = 0x8000 + BM(c ^ g0) - BM(c) per lane.  'swp' is
-// the thread's codeword relabelling: the butterflies of this thread that sit
-// at compile-time register k0 belong to group alpha(k0) ^ swp.
-template <class C>
-__device__ __forceinline__ void branch_metrics(const uint32_t (&Pk)[3], uint32_t swp,
+// decision constants kt[c] = 0x8000 + BM(c ^ g0) - BM(c) per lane.  sel[q]
+// is all-ones where this thread relabels code bit q: the butterfly at
+// compile-time register k0 belongs to group alpha(k0) ^ swp (see thread_swap).
+template <class C, bool SWAP>
+__device__ __forceinline__ void branch_metrics(const uint32_t (&Pk)[3], const uint32_t (&sel)[3],
                                                uint32_t (&bm)[C::NC], uint32_t (&kt)[C::NC]) {
   constexpr int R = C::R;
   uint32_t Pp[3], Mp[3];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     // lane value for code bit 1 is 127 + lambda (distance to -127), for bit 0
-    // it is 127 - lambda; relabelling by swp swaps the two.
-    uint32_t m1 = Pk[q], m0 = kLamMax2 - Pk[q];
-    uint32_t sel = 0u - ((swp >> (R - 1 - q)) & 1u);
-    Pp[q] = (m1 & ~sel) | (m0 & sel);
-    Mp[q] = (m0 & ~sel) | (m1 & sel);
+    // it is 127 - lambda
+    const uint32_t m1 = Pk[q], m0 = kLamMax2 - Pk[q];
+    if constexpr (SWAP) {
+      Pp[q] = (m1 & ~sel[q]) | (m0 & sel[q]);
+      Mp[q] = kLamMax2 - Pp[q];
+    } else {
+      Pp[q] = m1;
+      Mp[q] = m0;
+    }
   }
 #pragma unroll
   for (int c = 0; c < C::NC; ++c) {
@@ -200,38 +326,85 @@ __device__ __forceinline__ void branch_metrics(const uint32_t (&Pk)[3], uint32_t
   for (int c = 0; c < C::NC; ++c) kt[c] = bm[c ^ C::g0()] + kSignBias - bm[c];
 }
 
-// One trellis stage at phase PH for the thread's M registers (in place).
-template <class C, int T, int PH>
-__device__ __forceinline__ void acs_stage(uint32_t (&pm)[Shape<C, T>::M], uint32_t (&wd)[Shape<C, T>::W],
-                                          const uint32_t (&bm)[C::NC], const uint32_t (&kt)[C::NC]) {
-  using S = Shape<C, T>;
-  constexpr uint32_t g0 = C::g0(), gK = C::gK();
-  uint32_t tt[S::M];
-#pragma unroll
-  for (int k0 = 0; k0 < S::M; ++k0) {
-    if (k0 & (1 << PH)) continue;
-    const int k1 = k0 | (1 << PH);
-    const uint32_t al = C::alpha(rotr_v<C::v>((uint32_t)k0, PH));
-    const uint32_t be = al ^ gK;
-    const uint32_t X = pm[k0], Y = pm[k1];
-    const uint32_t c0 = X + bm[al], c1 = Y + bm[al ^ g0];
-    const uint32_t c2 = X + bm[be], c3 = Y + bm[be ^ g0];
-    tt[k0] = Y + kt[al] - X;
-    tt[k1] = Y + kt[be] - X;
-    pm[k0] = __vminu2(c0, c1);
-    pm[k1] = __vminu2(c2, c3);
-  }
-#pragma unroll
-  for (int w = 0; w < S::W; ++w) wd[w] = 0u;
-#pragma unroll
-  for (int k = 0; k < S::M; ++k) wd[k / S::B] = (wd[k / S::B] >> 1) | (tt[k] & kSignBias);
-  if (S::B < 16) {
-#pragma unroll
-    for (int w = 0; w < S::W; ++w) wd[w] >>= (16 - S::B);
+// Opaque constants that keep chosen additions on the FMA pipe (IMAD)
+// instead of the ALU pipe; passed in by the host so the compiler cannot fold
+// them.
+struct PipeConsts {
+  uint32_t one, minus_one;
+};
+
+__device__ __forceinline__ PipeConsts pipe_consts(const KArgs& a) {
+  PipeConsts k;
+  k.one = a.one;
+  k.minus_one = 0u - a.one;
+  return k;
+}
+
+// Byte masks of the four decisions of a butterfly: bytes 1 and 3 of t0 and
+// t1 hold the decisions in their sign bit; prmt with the sign-replicating
+// selector nibbles 9, B, D, F turns each into a 0x00 / 0xFF byte.
+__device__ __forceinline__ uint32_t decision_bytes(uint32_t t0, uint32_t t1) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, 0xFDB9;" : "=r"(r) : "r"(t0), "r"(t1));
+  return r;
+}
+
+// Merges the byte masks d[lo..lo+n) of consecutive butterflies into one
+// word: butterfly q's decisions end up at bit 7 - q of every byte.  The masks
+// are all-zero or all-one bytes, so a select with a constant needs no shift.
+template <int LO, int N>
+__device__ __forceinline__ uint32_t merge_decisions(const uint32_t* d) {
+  if constexpr (N == 1) {
+    return d[LO];
+  } else {
+    const uint32_t a = merge_decisions<LO, N / 2>(d);
+    const uint32_t b = merge_decisions<LO + N / 2, N / 2>(d);
+    constexpr uint32_t byte = ((1u << (N / 2)) - 1u) << (8 - LO - N);
+    constexpr uint32_t m = byte * 0x01010101u;
+    return (a & ~m) | (b & m);
   }
 }
 
-// Codeword relabelling of thread tau at phase ph (see branch_metrics).
+// One trellis stage at phase PH for the thread's M registers, in place.
+// Butterfly b (the b-th register k0 with bit PH clear, k1 = k0 | 1 << PH)
+// stores its four decision bits in survivor word b / BPW at bits 7 - q
+// (PB A of k0), 15 - q (PB B of k0), 23 - q (PB A of k1), 31 - q (PB B of
+// k1), q = b % BPW; a set bit means the upper branch was kept.
+// Per butterfly: two fused add-min (ALU), two candidate adds (FMA), one
+// decision difference on each pipe, one byte permute and 7/8 of a select
+// (ALU) for the decision bits.
+template <class C, int T, int PH>
+__device__ __forceinline__ void acs_stage(uint32_t (&pm)[Shape<C, T>::M], uint32_t (&wd)[Shape<C, T>::W],
+                                          const uint32_t (&bm)[C::NC], const uint32_t (&kt)[C::NC],
+                                          const PipeConsts& pc) {
+  using S = Shape<C, T>;
+  constexpr uint32_t g0 = C::g0(), gK = C::gK();
+#pragma unroll
+  for (int w = 0; w < S::W; ++w) {
+    uint32_t d[S::BPW];
+#pragma unroll
+    for (int q = 0; q < S::BPW; ++q) {
+      const int b = w * S::BPW + q;
+      const int k0 = ((b >> PH) << (PH + 1)) | (b & ((1 << PH) - 1));
+      const int k1 = k0 | (1 << PH);
+      const uint32_t al = C::alpha(rotr_v<C::v>((uint32_t)k0, PH));
+      const uint32_t be = al ^ gK;
+      const uint32_t X = pm[k0], Y = pm[k1];
+      const uint32_t c1 = Y * pc.one + bm[al ^ g0];
+      const uint32_t c3 = Y * pc.one + bm[be ^ g0];
+      const uint32_t t0 = Y + kt[al] - X;
+      const uint32_t t1 = X * pc.minus_one + (Y * pc.one + kt[be]);
+      pm[k0] = __viaddmin_s16x2(X, bm[al], c1);
+      pm[k1] = __viaddmin_s16x2(X, bm[be], c3);
+      d[q] = decision_bytes(t0, t1);
+    }
+    wd[w] = merge_decisions<0, S::BPW>(d);
+  }
+}
+
+// Codeword relabelling of thread tau at phase ph: the thread bits of the
+// physical index contribute alpha(rotr(tau << r, ph)) to every butterfly's
+// group (alpha is linear in the state bits).
 template <class C, int T>
 __device__ __forceinline__ uint32_t thread_swap(int tau, int ph) {
   using S = Shape<C, T>;
@@ -242,26 +415,6 @@ __device__ __forceinline__ uint32_t thread_swap(int tau, int ph) {
   return m;
 }
 
-// ------------------------------------------------------------- geometry --
-
-struct PbGeom {
-  int64_t f0, f1, o0, o1;
-  int delta;  // lock-step index of stage f0
-  int iend;   // lock-step index of stage f1
-};
-
-__device__ __forceinline__ PbGeom pb_geometry(int64_t n, int D, int L, int64_t b) {
-  PbGeom g;
-  int64_t s = b * D - L, e = (b + 1) * D + L;
-  g.f0 = s < 0 ? 0 : s;
-  g.f1 = (e < n ? e : n) - 1;
-  g.o0 = b * D;
-  g.o1 = (b + 1) * D < n ? (b + 1) * D : n;
-  g.delta = (int)(L - (g.o0 - g.f0));
-  g.iend = g.delta + (int)(g.f1 - g.f0);
-  return g;
-}
-
 // ------------------------------------------------------------- the kernel --
 
 template <class C, int T>
@@ -270,108 +423,435 @@ __device__ __forceinline__ void reinit_lane(uint32_t (&pm)[Shape<C, T>::M], int 
   using S = Shape<C, T>;
 #pragma unroll
   for (int k = 0; k < S::M; ++k) {
-    uint32_t init = known_start ? ((tau == 0 && k == 0) ? 0u : (kBigPM | (kBigPM << 16))) : 0u;
+    const uint32_t init = known_start ? ((tau == 0 && k == 0) ? 0u : (kBigPM | (kBigPM << 16))) : 0u;
     pm[k] = (pm[k] & ~lane_mask) | (init & lane_mask);
   }
 }
 
-// Work item of one group: which pair of PBs of which stream.
+// Work item of one group: a pair of PBs of one stream.
 struct PairWork {
   const int8_t* llr;
+  const int8_t* llr_end;
   uint8_t* out;
   int64_t n;       // stages of the stream
   int64_t bA;      // first PB of the pair
   bool hasB;       // second PB exists
 };
 
+// One period (P stages starting at lock-step index i0) of the forward pass.
+// CHECKED = false: every stage of the period is inside both PBs' forward
+// ranges (or B does not exist) and no re-initialisation falls inside.
+template <class C, int T, bool CHECKED, bool PUNCT>
+__device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], const uint32_t (&sel)[Shape<C, T>::P][3],
+                                               const KArgs& a, const int8_t* bufA, int cbA, const int8_t* bufB,
+                                               int cbB, bool hasB, int i0, int I, int L, int tau, PbRun& gA,
+                                               PbRun& gB, uint32_t*& gsv, int64_t rec_stride, uint32_t*& ssv,
+                                               bool smem_surv, const PipeConsts& pc) {
+  using S = Shape<C, T>;
+  constexpr int W = S::W;
+  constexpr int R = C::R;
+  // the soft values of the whole period, read and packed up front
+  uint32_t pkv[S::P][3];
+  if constexpr (!CHECKED && !PUNCT && R == 2) {
+    // both code bits of a stage in one 2-byte load (even offsets)
+    const uint16_t* pa = reinterpret_cast<const uint16_t*>(bufA + (gA.rel - cbA));
+    const uint16_t* pb = reinterpret_cast<const uint16_t*>(bufB + (gB.rel - cbB));
+#pragma unroll
+    for (int ph = 0; ph < S::P; ++ph) {
+      const uint32_t wa = pa[ph], wb = pb[ph];
+      uint32_t x0, x1;
+      asm("prmt.b32 %0, %1, %2, 0x6420;" : "=r"(x0) : "r"(wa), "r"(wb));
+      asm("prmt.b32 %0, %1, %2, 0x6521;" : "=r"(x1) : "r"(wa), "r"(wb));
+      pkv[ph][0] = __vmaxu2(x0 ^ 0x00800080u, 0x00010001u) - 0x00010001u;
+      pkv[ph][1] = __vmaxu2(x1 ^ 0x00800080u, 0x00010001u) - 0x00010001u;
+      pkv[ph][2] = 0u;
+    }
+    gA.rel += 2 * S::P;
+    gB.rel += 2 * S::P;
+  } else {
+#pragma unroll
+    for (int ph = 0; ph < S::P; ++ph) {
+      const int i = i0 + ph;
+      uint32_t ua[3] = {0u, 0u, 0u}, ub[3] = {0u, 0u, 0u};
+      const bool va = !CHECKED || (i < I && i >= gA.delta && i <= gA.iend);
+      const bool vb = hasB && (!CHECKED || (i < I && i >= gB.delta && i <= gB.iend));
+      if (va) read_raw<R, PUNCT>(a, gA, bufA, cbA, ua);
+      if (vb) read_raw<R, PUNCT>(a, gB, bufB, cbB, ub);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) pkv[ph][q] = q < R ? pack_soft(ua[q], ub[q]) : 0u;
+    }
+  }
+#pragma unroll
+  for (int ph = 0; ph < S::P; ++ph) {
+    const int i = i0 + ph;
+    if (CHECKED) {
+      if (i >= I) break;
+      if (i == gA.delta && i != 0) reinit_lane<C, T>(pm, tau, 0x0000ffffu, gA.known_start);
+      if (i == gB.delta && i != 0) reinit_lane<C, T>(pm, tau, 0xffff0000u, gB.known_start);
+    }
+    const uint32_t (&Pk)[3] = pkv[ph];
+    uint32_t bm[C::NC], kt[C::NC];
+    branch_metrics<C, (T > 1)>(Pk, sel[ph], bm, kt);
+    uint32_t wd[W];
+    // ph is a compile-time constant after unrolling
+    if constexpr (S::P > 0) if (ph == 0) acs_stage<C, T, 0>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 1) if (ph == 1) acs_stage<C, T, (S::P > 1 ? 1 : 0)>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 2) if (ph == 2) acs_stage<C, T, (S::P > 2 ? 2 : 0)>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 3) if (ph == 3) acs_stage<C, T, (S::P > 3 ? 3 : 0)>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 4) if (ph == 4) acs_stage<C, T, (S::P > 4 ? 4 : 0)>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 5) if (ph == 5) acs_stage<C, T, (S::P > 5 ? 5 : 0)>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 6) if (ph == 6) acs_stage<C, T, (S::P > 6 ? 6 : 0)>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 7) if (ph == 7) acs_stage<C, T, (S::P > 7 ? 7 : 0)>(pm, wd, bm, kt, pc);
+    if (i >= L) {
+      if (smem_surv) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) ssv[w] = wd[w];
+        ssv += S::RW;
+      } else {
+        uint32_t* d = gsv;
+        if constexpr (W % 4 == 0) {
+#pragma unroll
+          for (int w = 0; w < W; w += 4)
+            *reinterpret_cast<uint4*>(d + w) = make_uint4(wd[w], wd[w + 1], wd[w + 2], wd[w + 3]);
+        } else if constexpr (W == 2) {
+          *reinterpret_cast<uint2*>(d) = make_uint2(wd[0], wd[1]);
+        } else {
+          d[0] = wd[0];
+        }
+        gsv += rec_stride;
+      }
+    }
+  }
+}
+
+// Survivor bit of the state at physical index psi in a stage record at
+// phase mask lm = (1 << ph) - 1 (see acs_stage for the layout).
 template <class C, int T>
+__device__ __forceinline__ int record_bit(const uint32_t* __restrict__ rec, int psi, int lm, int x) {
+  using S = Shape<C, T>;
+  const int k = psi & (S::M - 1);
+  const int h = (k & (lm + 1)) ? 1 : 0;
+  const int b = ((k >> 1) & ~lm) | (k & lm);
+  const int word = (psi >> S::r) * S::W + (b >> S::LBPW);
+  const int bit = (((h << 1) | x) << 3) + 7 - (b & (S::BPW - 1));
+  return (rec[word] >> bit) & 1;
+}
+
+// ------------------------------------------------------------- traceback --
+
+// Traceback shape.  T == 1: the lane walks both PBs of its pair (two chains,
+// same records).  T >= 2: every lane walks one segment of one PB; a PB is
+// split into SPB segments of whole bytes, each non-top segment starting
+// LAMBDA records above its range from S_0 (a guess), then checked against
+// the exact exit state of the segment above and re-walked if it differs, so
+// the result is exact for any LAMBDA.
+template <class C, int T>
+struct TbShape {
+  static constexpr int RW = Shape<C, T>::RW;             // words per record
+  static constexpr int KR = tb_kr<C, T>();                // records per prefetch chunk
+  static constexpr int NBUF = tb_nbuf<C, T>();            // chunks in the per-lane ring
+  static constexpr int RING_WORDS = NBUF * KR * RW;       // per lane
+  static constexpr int LAMBDA = 8 * C::K;                 // warm-up records of a guessed segment
+};
+
+// One traceback step at a stage record rec (shared memory) for the state at
+// physical index psi; lm = (1 << ph) - 1 for the stage's phase ph.  In psi
+// coordinates the decoded bit is bit ph of psi and the predecessor replaces
+// that bit by the survivor bit; after phase 0 the index rotates into the
+// layout of the period before.  Returns the decoded bit.
+template <class C, int T>
+__device__ __forceinline__ int tb_step(int& psi, int& lm, int x, const uint32_t* rec) {
+  using S = Shape<C, T>;
+  constexpr int P = S::P;
+  constexpr int LMTOP = (1 << (P - 1)) - 1;
+  const int k = psi & (S::M - 1);
+  const int phb = lm + 1;
+  const int h = (k & phb) ? 1 : 0;
+  const int b = ((k >> 1) & ~lm) | (k & lm);
+  const int wi = (psi >> S::r) * S::W + (b >> S::LBPW);
+  const int bitpos = (((h << 1) | x) << 3) + 7 - (b & (S::BPW - 1));
+  const int upper = (rec[wi] >> bitpos) & 1;
+  const int np = (psi & ~phb) | (upper ? 0 : phb);
+  const bool wrap = (lm == 0);
+  psi = wrap ? (int)rotl_v<C::v>((uint32_t)np, P % C::v) : np;
+  lm = wrap ? LMTOP : (lm >> 1);
+  return h;
+}
+
+// Global address of survivor record j of the group.
+template <class C, int T>
+__device__ __forceinline__ const uint32_t* global_record(const KArgs& a, int64_t gslot, int j) {
+  return a.surv + ((int64_t)j * a.surv_pairs + gslot) * Shape<C, T>::RW;
+}
+
+// Walks records [lo, hs] of NCH chains (descending) and emits, for records
+// j <= emit_top[c], bit (j & 7) of output byte j >> 3 (bits of stages at or
+// beyond nout are cleared).  Records are read from shared memory: the
+// survivor region svs in shared-memory mode, else a per-lane ring that is
+// filled with cp.async KR records at a time.  On return psi is the exit
+// state and g the state held on arrival at record g_at.
+template <class C, int T, int NCH>
+__device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uint32_t* svs, uint32_t* ring,
+                                        int L, int hs, int lo, const int (&emit_top)[NCH], const int (&jend)[NCH],
+                                        const int (&x)[NCH], const int (&nout)[NCH], uint8_t* const (&dst)[NCH],
+                                        int g_at, int (&psi)[NCH], int (&g)[NCH]) {
+  using TS = TbShape<C, T>;
+  constexpr int P = Shape<C, T>::P, RW = TS::RW, KR = TS::KR, NBUF = TS::NBUF;
+  int lm[NCH];
+  uint32_t acc[NCH];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    lm[c] = (1 << ((L + min(hs, jend[c])) % P)) - 1;
+    acc[c] = 0u;
+    g[c] = 0;
+  }
+  if (hs < lo) return;
+  auto visit = [&](int j, const uint32_t* rec) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      if (j <= jend[c]) {
+        g[c] = (j == g_at) ? psi[c] : g[c];
+        const int bit = tb_step<C, T>(psi[c], lm[c], x[c], rec);
+        acc[c] = (acc[c] << 1) | (uint32_t)bit;
+        if ((j & 7) == 0 && j <= emit_top[c]) {
+          const int rem = nout[c] - j;
+          const uint32_t keep = rem >= 8 ? 0xffu : ((1u << (rem > 0 ? rem : 0)) - 1u);
+          // the last 8 steps shifted in stages j + 7 .. j: bit q is stage j + q
+          dst[c][j >> 3] = (uint8_t)(acc[c] & keep);
+        }
+      }
+    }
+  };
+  if (a.smem_surv) {
+    for (int j = hs; j >= lo; --j) visit(j, svs + j * RW);
+    return;
+  }
+  // ring: chunk ch holds records hs - ch*KR - q, q < KR, in buffer ch % NBUF
+  const int nchunk = (hs - lo) / KR + 1;
+  const int64_t stride = a.surv_pairs * (int64_t)RW;
+  const uint32_t* src_next = global_record<C, T>(a, gslot, hs);
+  int issued = 0;
+  auto issue = [&]() {
+    if (issued < nchunk) {
+      uint32_t* dst0 = ring + (issued % NBUF) * (KR * RW);
+      const int jtop = hs - issued * KR;
+#pragma unroll
+      for (int q = 0; q < KR; ++q) {
+        if (jtop - q >= lo) {
+          const unsigned d = (unsigned)__cvta_generic_to_shared(dst0 + q * RW);
+          if constexpr (RW >= 4) {
+#pragma unroll
+            for (int w = 0; w < RW; w += 4)
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 4 * w), "l"(src_next + w));
+          } else if constexpr (RW == 2) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src_next));
+          } else {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src_next));
+          }
+          src_next -= stride;
+        }
+      }
+    }
+    ++issued;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+#pragma unroll
+  for (int q = 0; q < NBUF - 1; ++q) issue();
+  for (int ch = 0; ch < nchunk; ++ch) {
+    issue();
+    asm volatile("cp.async.wait_group %0;" ::"n"(NBUF - 1) : "memory");
+    const int jtop = hs - ch * KR;
+    const int jbot = max(lo, jtop - KR + 1);
+    const uint32_t* buf = ring + (ch % NBUF) * (KR * RW);
+    for (int j = jtop; j >= jbot; --j) visit(j, buf + (jtop - j) * RW);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <class C, int T>
+__device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, const PbRun& gB, bool hasB, int J,
+                                               int64_t gslot, uint32_t* scratch, const uint32_t* svs) {
+  using TS = TbShape<C, T>;
+  const int L = a.L;
+  const int lane = threadIdx.x & 31;
+  const int tau = lane & (T - 1);
+  const unsigned gmask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(T - 1)));
+  __syncwarp(gmask);  // the forward pass's shared memory is reused by the ring
+  uint32_t* ring = scratch + tau * TS::RING_WORDS;
+  if constexpr (T == 1) {
+    // both PBs of the pair, exact walks from S_0 at their last stages
+    const int jA = gA.iend - L, jB = hasB ? gB.iend - L : -1;
+    const int emit_top[2] = {min(jA, gA.nout - 1), min(jB, gB.nout - 1)};
+    const int jend[2] = {jA, jB};
+    const int x[2] = {0, 1};
+    const int nout[2] = {gA.nout, gB.nout};
+    uint8_t* const dst[2] = {gA.dst, gB.dst};
+    int psi[2] = {0, 0}, g[2];
+    tb_walk<C, T, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
+  } else {
+    // lanes [0, SPB) walk PB A, [SPB, 2 SPB) walk PB B (all lanes walk A if
+    // there is no B); segment s covers records [s*len, (s+1)*len - 1]
+    const int SPB = hasB ? T / 2 : T;
+    const int xb = (hasB && tau >= SPB) ? 1 : 0;
+    const int s = tau - xb * SPB;
+    const PbRun& g0 = xb ? gB : gA;
+    const int jend = g0.iend - L;  // last record of this PB
+    const int seg = (((jend + 1 + SPB - 1) / SPB) + 7) & ~7;
+    const int lo = s * seg;
+    const int hi = min(jend, lo + seg - 1);
+    const int stop = jend / seg;    // top non-empty segment
+    const bool active = lo <= jend;
+    const int hs = (s == stop) ? jend : min(jend, hi + TS::LAMBDA);
+    int psi[1] = {0}, g[1] = {0};
+    {
+      const int emit_top[1] = {min(hi, g0.nout - 1)};
+      const int je[1] = {jend};
+      const int x[1] = {xb};
+      const int nout[1] = {g0.nout};
+      uint8_t* const dst[1] = {g0.dst};
+      if (active) tb_walk<C, T, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
+    }
+    // top-down check of the guessed segments of each PB in turn
+    for (int pb = 0; pb < (hasB ? 2 : 1); ++pb) {
+      const PbRun& gp = pb ? gB : gA;
+      const int jend_p = gp.iend - L;
+      const int seg_p = (((jend_p + 1 + SPB - 1) / SPB) + 7) & ~7;
+      const int top = jend_p / seg_p;
+      const int base = pb * SPB;
+      int exact = __shfl_sync(gmask, psi[0], base + top, T);
+      for (int q = top - 1; q >= 0; --q) {
+        const int gq = __shfl_sync(gmask, g[0], base + q, T);
+        int ex = __shfl_sync(gmask, psi[0], base + q, T);
+        if (gq != exact) {
+          // re-walk segment q from the exact state (rare)
+          if (tau == base + q) {
+            const int lo_q = q * seg_p, hi_q = min(jend_p, lo_q + seg_p - 1);
+            int p2 = exact;
+            int lm2 = (1 << ((L + hi_q) % Shape<C, T>::P)) - 1;
+            uint32_t acc2 = 0u;
+            for (int j = hi_q; j >= lo_q; --j) {
+              const uint32_t* rec = a.smem_surv ? svs + j * Shape<C, T>::RW : global_record<C, T>(a, gslot, j);
+              const int bit = tb_step<C, T>(p2, lm2, pb, rec);
+              if (j < gp.nout) {
+                acc2 |= (uint32_t)bit << (j & 7);
+                if ((j & 7) == 0) {
+                  gp.dst[j >> 3] = (uint8_t)acc2;
+                  acc2 = 0u;
+                }
+              }
+            }
+            psi[0] = p2;
+          }
+          ex = __shfl_sync(gmask, psi[0], base + q, T);
+        }
+        exact = ex;
+      }
+    }
+  }
+}
+
+template <class C, int T, bool PUNCT>
 __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, int64_t gslot,
                                             uint32_t* __restrict__ scratch, uint32_t* __restrict__ svs) {
   using S = Shape<C, T>;
   constexpr int R = C::R;
-  constexpr int M = S::M, W = S::W, P = S::P;
+  constexpr int M = S::M, P = S::P, CH = S::CH, RW = S::RW;
   const int lane = threadIdx.x & 31;
   const int tau = lane & (T - 1);
   const unsigned gmask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(T - 1)));
-  const int D = a.D, L = a.L;
+  const int L = a.L;
 
-  const PbGeom gA = pb_geometry(wk.n, D, L, wk.bA);
-  const PbGeom gB = wk.hasB ? pb_geometry(wk.n, D, L, wk.bA + 1) : gA;
+  PbRun gA = pb_run<R>(a, wk.llr, wk.out, wk.n, wk.bA);
+  PbRun gB = wk.hasB ? pb_run<R>(a, wk.llr, wk.out, wk.n, wk.bA + 1) : gA;
+  if (!wk.hasB) gB.iend = -1;
   const int I = max(gA.iend, gB.iend) + 1;  // lock-step stages
-  const int J = I - L;                      // stored survivor records (stages L..I-1)
+  const int J = I - L;                      // survivor records (stages L..I-1)
 
-  LlrReader rA, rB;
-  llr_init<R>(rA, a, gA.f0);
-  llr_init<R>(rB, a, gB.f0);
+  // soft-value staging: raw chunk c of PB A / B in buffer c & 1
+  constexpr int CB = raw_chunk_bytes<C>(CH);
+  int8_t* raw = reinterpret_cast<int8_t*>(scratch + raw_offset_words<C, T>());
+  const int nchunk = (I + CH - 1) / CH;
+  // relative value index at byte 0 of raw buffers 0 / 1 of PB A / B
+  int cbA0 = stage_raw_chunk<R, CH>(a, gA, wk.llr, wk.llr_end, 0, raw, tau, T);
+  int cbB0 = stage_raw_chunk<R, CH>(a, gB, wk.llr, wk.llr_end, 0, raw + CB, tau, T);
+  int cbA1 = 0, cbB1 = 0;
+  asm volatile("cp.async.commit_group;" ::: "memory");
 
-  uint32_t swp[P];
+  uint32_t sel[P][3];
 #pragma unroll
-  for (int ph = 0; ph < P; ++ph) swp[ph] = thread_swap<C, T>(tau, ph);
+  for (int ph = 0; ph < P; ++ph) {
+    const uint32_t m = thread_swap<C, T>(tau, ph);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sel[ph][q] = 0u - ((m >> (R - 1 - q)) & 1u);
+  }
 
   uint32_t pm[M];
 #pragma unroll
   for (int k = 0; k < M; ++k) pm[k] = 0u;
-  if (gA.delta == 0) reinit_lane<C, T>(pm, tau, 0x0000ffffu, gA.f0 == 0);
-  if (gB.delta == 0) reinit_lane<C, T>(pm, tau, 0xffff0000u, gB.f0 == 0);
+  if (gA.delta == 0) reinit_lane<C, T>(pm, tau, 0x0000ffffu, gA.known_start);
+  if (gB.delta == 0 && wk.hasB) reinit_lane<C, T>(pm, tau, 0xffff0000u, gB.known_start);
+  // periods [fast_lo, fast_hi] need no per-stage checks
+  const int dmax = max(gA.delta, gB.delta);
+  const int fast_lo = dmax + (dmax > 0 ? 1 : 0);
+  const bool fast_ok = wk.hasB && (PUNCT || R != 2 || ((reinterpret_cast<uintptr_t>(wk.llr) & 1) == 0));
+  const int fast_hi = fast_ok ? min(gA.iend, gB.iend) - (P - 1) : -1;
 
-  int64_t rec_stride = a.surv_pairs * (int64_t)(T * W);  // global: words per record row
-  uint32_t* gsv = a.surv + gslot * (T * W) + tau * W;
-  uint32_t* ssv = svs + tau * W;
+  const int64_t rec_stride = a.surv_pairs * (int64_t)RW;  // global: words per record row
+  uint32_t* gsv = a.surv + gslot * RW + tau * S::W;
+  uint32_t* ssv = svs + tau * S::W;
 
+  const PipeConsts pc = pipe_consts(a);
   int since_renorm = 0;
   for (int i0 = 0; i0 < I; i0 += P) {
-#pragma unroll
-    for (int ph = 0; ph < P; ++ph) {
-      const int i = i0 + ph;
-      if (i < I) {
-        if (i == gA.delta && i != 0) reinit_lane<C, T>(pm, tau, 0x0000ffffu, gA.f0 == 0);
-        if (i == gB.delta && i != 0 && wk.hasB) reinit_lane<C, T>(pm, tau, 0xffff0000u, gB.f0 == 0);
-        int pa[3] = {127, 127, 127}, pb[3] = {127, 127, 127};
-        if (i >= gA.delta && i <= gA.iend) llr_next<R>(rA, a, wk.llr, pa);
-        if (wk.hasB && i >= gB.delta && i <= gB.iend) llr_next<R>(rB, a, wk.llr, pb);
-        uint32_t Pk[3];
-#pragma unroll
-        for (int q = 0; q < R; ++q) Pk[q] = (uint32_t)pa[q] | ((uint32_t)pb[q] << 16);
-        uint32_t bm[C::NC], kt[C::NC];
-        branch_metrics<C>(Pk, swp[ph], bm, kt);
-        uint32_t wd[W];
-        // ph is a compile-time constant after unrolling; dispatch to the
-        // matching in-place stage.
-        switch (ph) {
-          case 0: acs_stage<C, T, 0>(pm, wd, bm, kt); break;
-          case 1: if constexpr (P > 1) acs_stage<C, T, (P > 1 ? 1 : 0)>(pm, wd, bm, kt); break;
-          case 2: if constexpr (P > 2) acs_stage<C, T, (P > 2 ? 2 : 0)>(pm, wd, bm, kt); break;
-          case 3: if constexpr (P > 3) acs_stage<C, T, (P > 3 ? 3 : 0)>(pm, wd, bm, kt); break;
-          case 4: if constexpr (P > 4) acs_stage<C, T, (P > 4 ? 4 : 0)>(pm, wd, bm, kt); break;
-          case 5: if constexpr (P > 5) acs_stage<C, T, (P > 5 ? 5 : 0)>(pm, wd, bm, kt); break;
-          case 6: if constexpr (P > 6) acs_stage<C, T, (P > 6 ? 6 : 0)>(pm, wd, bm, kt); break;
-          case 7: if constexpr (P > 7) acs_stage<C, T, (P > 7 ? 7 : 0)>(pm, wd, bm, kt); break;
-          default: break;
-        }
-        if (i >= L) {
-          const int j = i - L;
-          if (a.smem_surv) {
-            uint32_t* d = ssv + j * (T * W);
-#pragma unroll
-            for (int w = 0; w < W; ++w) d[w] = wd[w];
-          } else {
-            uint32_t* d = gsv + (int64_t)j * rec_stride;
-            if constexpr (W % 4 == 0) {
-#pragma unroll
-              for (int w = 0; w < W; w += 4)
-                *reinterpret_cast<uint4*>(d + w) = make_uint4(wd[w], wd[w + 1], wd[w + 2], wd[w + 3]);
-            } else if constexpr (W == 2) {
-              *reinterpret_cast<uint2*>(d) = make_uint2(wd[0], wd[1]);
-            } else {
-              d[0] = wd[0];
-            }
-          }
-        }
+    if (i0 % CH == 0) {
+      // chunk c begins: its raw bytes were requested one chunk ago; request
+      // chunk c + 1 into the buffer chunk c - 1 used (every lane is past it)
+      const int c = i0 / CH;
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncwarp(gmask);
+      if (c + 1 < nchunk) {
+        const int nb = (c + 1) & 1;
+        const int na = stage_raw_chunk<R, CH>(a, gA, wk.llr, wk.llr_end, c + 1, raw + nb * 2 * CB, tau, T);
+        const int nbb = stage_raw_chunk<R, CH>(a, gB, wk.llr, wk.llr_end, c + 1, raw + nb * 2 * CB + CB, tau, T);
+        if (nb) { cbA1 = na; cbB1 = nbb; } else { cbA0 = na; cbB0 = nbb; }
       }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     }
+    const int cur = (i0 / CH) & 1;
+    const int8_t* bufA = raw + cur * 2 * CB;
+    const int8_t* bufB = bufA + CB;
+    const int cbA = cur ? cbA1 : cbA0, cbB = cur ? cbB1 : cbB0;
+    if (i0 >= fast_lo && i0 <= fast_hi)
+      forward_period<C, T, false, PUNCT>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA, gB, gsv,
+                                         rec_stride, ssv, a.smem_surv, pc);
+    else
+      forward_period<C, T, true, PUNCT>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA, gB, gsv,
+                                        rec_stride, ssv, a.smem_surv, pc);
     if (i0 + P < I) {
       // end of a full period: transpose back to psi = u (T > 1)
-      if constexpr (T > 1) {
+      if constexpr (vector_transpose<C, T>()) {
+        // state u = (tau' << r) | k' comes from thread k' mod T, register
+        // (tau' << (r - t)) | (k' >> t)
+        constexpr int MT = M / T, STR = M + 4;
+        __syncwarp(gmask);
+        uint32_t* mine = scratch + tau * STR;
+#pragma unroll
+        for (int k = 0; k < M; k += 4)
+          *reinterpret_cast<uint4*>(mine + k) = make_uint4(pm[k], pm[k + 1], pm[k + 2], pm[k + 3]);
+        __syncwarp(gmask);
+#pragma unroll
+        for (int w = 0; w < T; ++w) {
+          const uint32_t* src = scratch + w * STR + tau * MT;
+#pragma unroll
+          for (int m = 0; m < MT; m += 4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(src + m);
+            pm[(m + 0) * T + w] = q.x;
+            pm[(m + 1) * T + w] = q.y;
+            pm[(m + 2) * T + w] = q.z;
+            pm[(m + 3) * T + w] = q.w;
+          }
+        }
+      } else if constexpr (T > 1) {
         __syncwarp(gmask);
 #pragma unroll
         for (int k = 0; k < M; ++k) scratch[(k << S::t) | tau] = pm[k];
@@ -380,11 +860,11 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
         if constexpr (M >= 4) {
 #pragma unroll
           for (int k = 0; k < M; k += 4) {
-            uint4 q = *reinterpret_cast<const uint4*>(src + k);
+            const uint4 q = *reinterpret_cast<const uint4*>(src + k);
             pm[k] = q.x; pm[k + 1] = q.y; pm[k + 2] = q.z; pm[k + 3] = q.w;
           }
         } else {
-          uint2 q = *reinterpret_cast<const uint2*>(src);
+          const uint2 q = *reinterpret_cast<const uint2*>(src);
           pm[0] = q.x; pm[1] = q.y;
         }
       }
@@ -393,113 +873,18 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
         uint32_t ref = pm[0];
         if constexpr (T > 1) ref = __shfl_sync(gmask, ref, 0, T);
 #pragma unroll
-        for (int k = 0; k < M; ++k) pm[k] = pm[k] + kRenormBase - ref;
+        for (int k = 0; k < M; ++k) pm[k] = pm[k] + S::RENORM_BASE - ref;
       }
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 
-  // ---------------------------------------------------------- traceback --
-  // Tracer lanes: T == 1: lane walks both PBs; T >= 2: tau 0 -> A, tau 1 -> B.
-  constexpr int NCH = (T == 1) ? 2 : 1;
-  const bool tracer = (T == 1) || (tau == 0) || (tau == 1 && wk.hasB);
-  int psi[NCH], ph[NCH], iend[NCH], nout[NCH];
-  int64_t obyte[NCH];
-  uint32_t acc[NCH];
-  int shift[NCH];
-#pragma unroll
-  for (int c = 0; c < NCH; ++c) {
-    const int x = (T == 1) ? c : (tau & 1);
-    const PbGeom& g = x ? gB : gA;
-    psi[c] = 0;
-    iend[c] = (x == 1 && !wk.hasB) ? -1 : g.iend;
-    ph[c] = (iend[c] >= 0) ? (iend[c] % P) : 0;
-    nout[c] = (int)(g.o1 - g.o0);
-    obyte[c] = g.o0 >> 3;
-    acc[c] = 0u;
-    shift[c] = x ? 16 : 0;
-  }
-
-  auto walk = [&](int j, const uint32_t* __restrict__ rec) {
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const int i = j + L;
-      if (i <= iend[c]) {
-        const int p = psi[c];
-        const uint32_t w = rec[p >> S::LB];
-        const int kept_upper = (w >> (shift[c] + (p & (S::B - 1)))) & 1;
-        const int bit = (p >> ph[c]) & 1;
-        int np = (p & ~(1 << ph[c])) | ((kept_upper ^ 1) << ph[c]);
-        if (ph[c] == 0) {
-          np = (int)rotl_v<C::v>((uint32_t)np, P % C::v);
-          ph[c] = P - 1;
-        } else {
-          --ph[c];
-        }
-        psi[c] = np;
-        const int pos = j;  // lock-step index i = L + pos, output stage o0 + pos
-        if (pos < nout[c]) {
-          acc[c] |= (uint32_t)bit << (pos & 7);
-          if ((pos & 7) == 0) {
-            wk.out[obyte[c] + (pos >> 3)] = (uint8_t)acc[c];
-            acc[c] = 0u;
-          }
-        }
-      }
-    }
-  };
-
-  if (a.smem_surv) {
-    __syncwarp(gmask);
-    if (tracer) {
-      for (int j = J - 1; j >= 0; --j) walk(j, svs + j * (T * W));
-    }
-  } else {
-    // Double-buffered ring of kRing records per chunk, filled by all T lanes
-    // with cp.async, walked by the tracer lanes.
-    const int nchunks = (J + kRing - 1) / kRing;
-    auto issue = [&](int c, int buf) {
-      uint32_t* dst0 = scratch + buf * (kRing * T * W) + tau * W;
-      for (int q = 0; q < kRing; ++q) {
-        const int j = J - 1 - c * kRing - q;
-        if (j < 0) break;
-        const uint32_t* src = a.surv + ((int64_t)j * a.surv_pairs + gslot) * (T * W) + tau * W;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(dst0 + q * (T * W));
-#pragma unroll
-        for (int w = 0; w < W; w += (W >= 4 ? 4 : W)) {
-          if constexpr (W >= 4)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 4 * w), "l"(src + w));
-          else if constexpr (W == 2)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src));
-          else
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src));
-        }
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    __syncwarp(gmask);
-    if (nchunks > 0) issue(0, 0);
-    for (int c = 0; c < nchunks; ++c) {
-      if (c + 1 < nchunks) {
-        issue(c + 1, (c + 1) & 1);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-      } else {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-      }
-      __syncwarp(gmask);
-      if (tracer) {
-        const uint32_t* ring = scratch + (c & 1) * (kRing * T * W);
-        const int jhi = J - 1 - c * kRing;
-        const int jlo = max(0, jhi - kRing + 1);
-        for (int j = jhi; j >= jlo; --j) walk(j, ring + (jhi - j) * (T * W));
-      }
-      __syncwarp(gmask);
-    }
-  }
+  traceback_pair<C, T>(a, gA, gB, wk.hasB, J, gslot, scratch, svs);
 }
 
 // Plain launch: pair p of one stream.
-template <class C, int T>
-__global__ void __launch_bounds__(256) pbvd_decode_kernel(const KArgs a) {
+template <class C, int T, bool PUNCT>
+__global__ void __launch_bounds__(256, 1) pbvd_decode_kernel(const KArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int groups_per_cta = blockDim.x / T;
   const int gl = threadIdx.x / T;
@@ -510,11 +895,12 @@ __global__ void __launch_bounds__(256) pbvd_decode_kernel(const KArgs a) {
   uint32_t* svs = smem + groups_per_cta * SW + (int64_t)gl * a.smem_rec_words;
   PairWork wk;
   wk.llr = a.llr;
+  wk.llr_end = a.llr + a.llr_count;
   wk.out = a.out;
   wk.n = a.n;
   wk.bA = 2 * pair;
   wk.hasB = (2 * pair + 1) < a.n_blocks;
-  decode_pair<C, T>(a, wk, pair, scratch, svs);
+  decode_pair<C, T, PUNCT>(a, wk, pair, scratch, svs);
 }
 
 }  // namespace pbvd

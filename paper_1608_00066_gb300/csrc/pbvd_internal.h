@@ -21,7 +21,10 @@ struct KArgs {
   int32_t smem_rec_words; // shared-memory record words per group (smem mode)
   int32_t punct_P;        // 0: not punctured, else pattern period
   int32_t punct_C;        // values sent per period
+  int64_t llr_count;      // soft values readable at llr
+  uint32_t one;           // the value 1, opaque to the compiler (pipe balancing)
   int16_t punct_off[32 * 4];  // [col][r]: offset in the period, -1 = punctured
+  int16_t punct_pre[33];      // values sent in the columns before col
 };
 
 // Batched work: one entry per pair of PBs.
@@ -49,6 +52,7 @@ struct KernelEntry {
   int K, R;
   uint32_t gens[3];
   int T;
+  bool punct;              // built for punctured input
   int words_per_stage;     // survivor record words per stage per pair (T * W)
   int scratch_words;       // shared-memory words per group besides records
   LaunchFn launch;

@@ -81,7 +81,7 @@ def test_cta_shapes():
     f = synth.make_frame(spec, 20000, 2.0, seed=5)
     want = oracle_bits(spec, f.llr, f.n_stages, 256, 42)
     dec = make_decoder(spec, 256, 42)
-    for T, cta in ((1, 32), (1, 64), (1, 256), (2, 128), (4, 96), (8, 256), (32, 64)):
+    for T, cta in ((1, 32), (1, 64), (1, 128), (2, 128), (4, 96), (8, 256), (32, 64)):
         got = gpu_bits(dec, f.llr, f.n_stages, threads_per_pair=T, cta_threads=cta, survivors_in_smem=0)
         assert np.array_equal(got, want), (T, cta)
 
