@@ -138,6 +138,31 @@ PBVD_API int pbvd_set_config(pbvd_ctx *ctx, const pbvd_config *cfg);
 /* Reads back the configuration pbvd_decode would use for n_stages. */
 PBVD_API int pbvd_get_config(const pbvd_ctx *ctx, size_t n_stages, pbvd_config *cfg);
 
+/* Allocation-free variant of pbvd_decode (no counterpart in the paper).
+ * For callers that must not allocate device memory while decoding: code
+ * running under CUDA stream capture, real-time receive chains that reserve
+ * all memory up front, hosts whose device memory belongs to their own pool.
+ * pbvd_decode grows a context workspace with cudaMalloc; this call instead
+ * keeps the survivor bits in one fixed array of
+ * pbvd_noalloc_max_survivor_bytes() bytes (16 MiB) that every GPU loading the
+ * library holds until exit, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Arguments and results are those of pbvd_decode; the
+ * survivor bits always live in that array (the context's survivors_in_smem
+ * setting is ignored).
+ * With an automatic configuration it uses fewer threads per pair of blocks
+ * (smaller survivor records) when that is what makes the bits fit.  Returns
+ * PBVD_EINVAL when the launch would still need more survivor bytes than the
+ * array holds (for the K=7 rate-1/2 code with D=512, L=42: about 1.9 million
+ * stages) or when the current device is not the context's.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make it outside stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it. */
+PBVD_API int pbvd_decode_noalloc(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
+                                 uint8_t *d_out, void *stream);
+
+/* Size of the fixed survivor array of pbvd_decode_noalloc, in bytes. */
+PBVD_API size_t pbvd_noalloc_max_survivor_bytes(void);
+
 /* Message for an error code (static string). */
 PBVD_API const char *pbvd_strerror(int code);
 

@@ -353,3 +353,112 @@ int pbvd_decode_batch(const pbvd_batch_item* items, size_t n_items, void* stream
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free decode.
+//
+// Some callers must not allocate device memory while they decode: code that
+// runs inside CUDA stream capture (an allocation there either fails or
+// breaks the capture), real-time receive chains that reserve all memory at
+// start-up and forbid allocation on the data path, and hosts whose device
+// memory belongs to their own pool allocator.  pbvd_decode grows a per-context
+// workspace with cudaMalloc on first use of a larger size; this variant keeps
+// the survivor bits in one fixed array that is part of the library's device
+// image instead, and calls no allocation routine.
+//
+// The array is file-scope device memory: every GPU that loads the library
+// holds kNoAllocSurvivorBytes of it until the process exits.  Host code may
+// not use the array's name as an address (on the host it is only a
+// stand-in), so its device address is looked up once per device with
+// cudaGetSymbolAddress while that device is current, and passed to the
+// kernel.  That lookup happens on the first call on each device, so make the
+// first call outside any stream capture.  All calls share the array and it
+// keeps the last call's contents: nothing needs clearing (every survivor word
+// the traceback reads is written earlier in the same launch), but calls whose
+// work overlaps on the GPU race on it.
+
+namespace {
+
+constexpr size_t kNoAllocSurvivorBytes = size_t(16) << 20;  // 16 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) uint32_t g_noalloc_survivors[kNoAllocSurvivorBytes / sizeof(uint32_t)];
+
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the survivor array on the current device (looked up once).
+int noalloc_survivors(int device, uint32_t** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return PBVD_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_survivors);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_noalloc_ptr[device] = static_cast<uint32_t*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return PBVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_out, void* stream) {
+  if (!c || !d_llr || !d_out || n_stages == 0) return PBVD_EINVAL;
+  if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
+  int dev = -1;
+  PBVD_CUDA(cudaGetDevice(&dev));
+  if (dev != c->device) return PBVD_EINVAL;
+  // the survivor bits always live in the fixed array here
+  pbvd_ctx cc = *c;
+  cc.cfg.survivors_in_smem = 0;
+  Plan p;
+  int rc = plan_decode(&cc, n_stages, &p);
+  if (rc != PBVD_OK) return rc;
+  // with an automatic thread count, fall back to fewer threads per pair
+  // (smaller survivor records) until the survivor bits fit the array
+  while (c->cfg.threads_per_pair == 0 && p.surv_bytes > kNoAllocSurvivorBytes && p.T > 1) {
+    cc.cfg.threads_per_pair = p.T / 2;
+    if (find_entry(c->K, c->R, c->gens, cc.cfg.threads_per_pair, c->P != 0) < 0) break;
+    rc = plan_decode(&cc, n_stages, &p);
+    if (rc != PBVD_OK) return rc;
+  }
+  if (p.surv_bytes > kNoAllocSurvivorBytes) return PBVD_EINVAL;
+  uint32_t* surv = nullptr;
+  rc = noalloc_survivors(dev, &surv);
+  if (rc != PBVD_OK) return rc;
+  rc = grant_smem(p.entry, p.smem_bytes);
+  if (rc != PBVD_OK) return rc;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.llr = d_llr;
+  a.out = d_out;
+  a.surv = surv;
+  a.n = (int64_t)n_stages;
+  a.n_blocks = p.n_blocks;
+  a.n_pairs = p.n_pairs;
+  a.surv_pairs = p.n_pairs;
+  a.D = c->D;
+  a.L = c->L;
+  a.smem_surv = 0;
+  a.smem_rec_words = 0;
+  a.punct_P = c->P;
+  a.punct_C = c->punct_C;
+  std::memcpy(a.punct_off, c->punct_off, sizeof(a.punct_off));
+  std::memcpy(a.punct_pre, c->punct_pre, sizeof(a.punct_pre));
+  size_t cnt = 0;
+  pbvd_llr_count(c, n_stages, &cnt);
+  a.llr_count = (int64_t)cnt;
+  a.one = 1u;
+  const int64_t grid = ceil_div(p.n_pairs, p.groups);
+  if (grid > 0x7fffffff) return PBVD_EINVAL;
+  const KernelEntry& e = registry().entries[p.entry];
+  PBVD_CUDA(e.launch(a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
+  return PBVD_OK;
+}
+
+size_t pbvd_noalloc_max_survivor_bytes(void) { return kNoAllocSurvivorBytes; }
+
+}  // extern "C"

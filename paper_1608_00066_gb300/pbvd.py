@@ -32,6 +32,7 @@ PBVD_EBUSY = -6
 EXPORTS = (
     "pbvd_create", "pbvd_destroy", "pbvd_decode", "pbvd_llr_count", "pbvd_decode_batch",
     "pbvd_set_config", "pbvd_get_config", "pbvd_strerror", "pbvd_last_cuda_error",
+    "pbvd_decode_noalloc", "pbvd_noalloc_max_survivor_bytes",
 )
 
 
@@ -93,6 +94,10 @@ def load(path: Optional[str] = None):
         lib.pbvd_strerror.restype = ctypes.c_char_p
         lib.pbvd_last_cuda_error.argtypes = []
         lib.pbvd_last_cuda_error.restype = ctypes.c_char_p
+        lib.pbvd_decode_noalloc.argtypes = [V, V, SZ, V, V]
+        lib.pbvd_decode_noalloc.restype = I
+        lib.pbvd_noalloc_max_survivor_bytes.argtypes = []
+        lib.pbvd_noalloc_max_survivor_bytes.restype = SZ
         _lib = lib
         return lib
 
@@ -130,6 +135,16 @@ def pbvd_destroy(ctx: int) -> None:
 
 def pbvd_decode(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0) -> None:
     _check(load().pbvd_decode(ctx, d_llr, n_stages, d_out, stream or None), "pbvd_decode")
+
+
+def pbvd_decode_noalloc(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0) -> None:
+    """pbvd_decode without any device allocation: the survivor bits live in a
+    fixed array inside the library (see include/pbvd.h)."""
+    _check(load().pbvd_decode_noalloc(ctx, d_llr, n_stages, d_out, stream or None), "pbvd_decode_noalloc")
+
+
+def pbvd_noalloc_max_survivor_bytes() -> int:
+    return int(load().pbvd_noalloc_max_survivor_bytes())
 
 
 def pbvd_llr_count(ctx: int, n_stages: int) -> int:
