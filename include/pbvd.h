@@ -113,11 +113,34 @@ typedef struct pbvd_batch_item {
 } pbvd_batch_item;
 
 /* Decodes n_items independent frames of possibly different codes and lengths
- * in one persistent kernel launch.  Each frame's result equals pbvd_decode
- * on that frame alone with the same context.  items is a host array read
- * during the call; the work list is uploaded into a workspace owned by the
- * first item's context.  Output ranges must not overlap. */
+ * in one persistent kernel launch (batching is not in the paper; every frame
+ * is decoded exactly as pbvd_decode decodes it alone with its context).
+ * One launch covers the K=7 (171,133) rate-1/2 code, the same code punctured
+ * (any pattern) and the K=9 (557,663,711) rate-1/3 code; contexts of the same
+ * code must agree on D, L and the puncture pattern (PBVD_EINVAL otherwise),
+ * other codes give PBVD_EUNSUPPORTED.  items is a host array read during the
+ * call.  The work list (blocks of all frames grouped by code, sorted by
+ * length, paired and cut into tiles taken from a device queue) is built on the
+ * host and uploaded into a workspace owned by the first item's context, which
+ * must therefore not be used by another batch still in flight.  Output ranges
+ * must not overlap. */
 PBVD_API int pbvd_decode_batch(const pbvd_batch_item *items, size_t n_items, void *stream);
+
+/* A prepared batch: the work list and workspace of pbvd_decode_batch, kept so
+ * that the decode itself is one memset and one kernel launch (pbvd_batch_run),
+ * which can be captured in a CUDA graph and replayed.  The item buffers must
+ * stay valid and keep their addresses while the batch is in use. */
+typedef struct pbvd_batch pbvd_batch;
+
+/* Builds and uploads (on stream) the work list of items into a new batch. */
+PBVD_API int pbvd_batch_prepare(pbvd_batch **out, const pbvd_batch_item *items, size_t n_items,
+                                void *stream);
+
+/* Decodes a prepared batch: resets the tile queue and launches the kernel. */
+PBVD_API int pbvd_batch_run(pbvd_batch *batch, void *stream);
+
+/* Frees a batch (synchronises the device first).  NULL is ignored. */
+PBVD_API void pbvd_batch_destroy(pbvd_batch *batch);
 
 /* Kernel configuration of a context (the tuning knobs).
  *   threads_per_pair  T: threads that share one pair of blocks (power of two,

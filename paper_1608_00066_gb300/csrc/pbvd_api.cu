@@ -35,6 +35,8 @@ int cuda_fail(cudaError_t e) {
 struct Registry {
   std::vector<KernelEntry> entries;
   std::vector<int> smem_set;  // max dynamic smem already granted per entry
+  std::vector<BatchKernelEntry> batch;
+  std::vector<int> batch_smem_set;
 };
 
 Registry& registry() {
@@ -48,6 +50,10 @@ Registry& registry() {
     n += register_small(buf + n, 64 - n);
     reg.entries.assign(buf, buf + n);
     reg.smem_set.assign(n, 48 * 1024);
+    BatchKernelEntry bb[4];
+    const int nb = register_batch(bb, 4);
+    reg.batch.assign(bb, bb + nb);
+    reg.batch_smem_set.assign(nb, 48 * 1024);
   });
   return reg;
 }
@@ -90,6 +96,7 @@ struct pbvd_ctx {
   int smem_optin;
   void* work;
   size_t work_bytes;
+  pbvd_batch* batch;  // work list of the last pbvd_decode_batch led by this context
 };
 
 namespace {
@@ -181,6 +188,233 @@ int grant_smem(int entry, size_t bytes) {
 
 }  // namespace
 
+// -------------------------------------------------------------- batches --
+
+struct pbvd_batch {
+  int device;
+  int entry;            // combined kernel
+  int grid, cta;
+  size_t smem;
+  BatchArgs args;
+  BatchPair* d_pairs;
+  size_t pairs_cap;     // elements
+  BatchTile* d_tiles;
+  size_t tiles_cap;
+  int32_t* d_counter;
+  uint32_t* d_surv;
+  size_t surv_bytes;
+};
+
+namespace {
+
+struct HostPb {
+  int item;
+  int64_t b;
+  int len;    // forward stages f1 - f0 + 1
+};
+
+// Forward length of block b of an n-stage stream (Sec. III-A geometry).
+int block_len(int64_t n, int D, int L, int64_t b) {
+  const int64_t s = b * D - L, e = (b + 1) * D + L;
+  const int64_t f0 = s < 0 ? 0 : s;
+  const int64_t f1 = (e < n ? e : n) - 1;
+  return (int)(f1 - f0 + 1);
+}
+
+template <class T>
+int grow(T** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return PBVD_OK;
+  if (*p) {
+    cudaError_t e = cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  const size_t n = need > 0 ? need : 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e);
+  }
+  *cap = n;
+  return PBVD_OK;
+}
+
+// Builds the work list of a batch into b (created if null): blocks of every
+// frame grouped by code slot, sorted by forward length and paired, cut into
+// tiles of one CTA's pairs, tiles ordered longest first.  Uploads it on
+// 'stream'.
+int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd_batch* reuse, pbvd_batch** out) {
+  Registry& reg = registry();
+  if (reg.batch.empty()) return PBVD_EUNSUPPORTED;
+  const int entry = 0;
+  const BatchKernelEntry& be = reg.batch[entry];
+  // map items to code slots; the contexts of a slot must agree on D, L and
+  // the puncture pattern
+  const pbvd_ctx* slot_ctx[kBatchSlots] = {nullptr, nullptr, nullptr};
+  std::vector<int> item_slot(n_items);
+  for (size_t i = 0; i < n_items; ++i) {
+    const pbvd_batch_item& it = items[i];
+    if (!it.ctx || !it.d_llr || !it.d_out || it.n_stages == 0 || it.n_stages > ((size_t)1 << 40))
+      return PBVD_EINVAL;
+    const pbvd_ctx* c = it.ctx;
+    int slot = -1;
+    for (int s = 0; s < kBatchSlots && slot < 0; ++s) {
+      if (be.K[s] != c->K || be.R[s] != c->R || be.punct[s] != (c->P != 0)) continue;
+      bool same = true;
+      for (int r = 0; r < c->R; ++r) same = same && be.gens[s][r] == c->gens[r];
+      if (same) slot = s;
+    }
+    if (slot < 0) return PBVD_EUNSUPPORTED;
+    if (!slot_ctx[slot]) {
+      slot_ctx[slot] = c;
+    } else {
+      const pbvd_ctx* r0 = slot_ctx[slot];
+      if (r0->D != c->D || r0->L != c->L || r0->P != c->P || r0->device != c->device) return PBVD_EINVAL;
+      if (r0->P && std::memcmp(r0->punct_off, c->punct_off, sizeof(c->punct_off)) != 0) return PBVD_EINVAL;
+    }
+    item_slot[i] = slot;
+  }
+  const pbvd_ctx* c0 = items[0].ctx;
+  int dev = -1;
+  PBVD_CUDA(cudaGetDevice(&dev));
+  if (dev != c0->device) return PBVD_EINVAL;
+
+  // blocks per slot, longest forward range first, paired neighbours
+  std::vector<HostPb> pbs[kBatchSlots];
+  for (size_t i = 0; i < n_items; ++i) {
+    const pbvd_ctx* c = items[i].ctx;
+    const int64_t n = (int64_t)items[i].n_stages;
+    const int64_t nb = ceil_div(n, c->D);
+    for (int64_t b = 0; b < nb; ++b) pbs[item_slot[i]].push_back({(int)i, b, block_len(n, c->D, c->L, b)});
+  }
+  const int cta = 64;
+  std::vector<BatchPair> pairs;
+  std::vector<BatchTile> tiles;
+  std::vector<int> tile_cost;
+  for (int s = 0; s < kBatchSlots; ++s) {
+    std::vector<HostPb>& v = pbs[s];
+    if (v.empty()) continue;
+    std::stable_sort(v.begin(), v.end(), [](const HostPb& x, const HostPb& y) { return x.len > y.len; });
+    const int groups = cta / be.T[s];
+    const int64_t first_pair = (int64_t)pairs.size();
+    for (size_t k = 0; k < v.size(); k += 2) {
+      BatchPair p;
+      std::memset(&p, 0, sizeof(p));
+      for (int h = 0; h < 2; ++h) {
+        const HostPb& q = v[k + (k + h < v.size() ? h : 0)];
+        const pbvd_batch_item& it = items[q.item];
+        size_t cnt = 0;
+        pbvd_llr_count(it.ctx, it.n_stages, &cnt);
+        p.llr[h] = it.d_llr;
+        p.llr_end[h] = it.d_llr + cnt;
+        p.out[h] = it.d_out;
+        p.n[h] = (int64_t)it.n_stages;
+        p.b[h] = q.b;
+      }
+      p.hasB = (k + 1 < v.size()) ? 1 : 0;
+      pairs.push_back(p);
+    }
+    const int64_t np = (int64_t)pairs.size() - first_pair;
+    for (int64_t t = 0; t < np; t += groups) {
+      BatchTile tl;
+      tl.slot = s;
+      tl.count = (int)std::min<int64_t>(groups, np - t);
+      tl.first = first_pair + t;
+      tiles.push_back(tl);
+      // pairs are sorted, so the tile's first pair is its longest
+      tile_cost.push_back(v[2 * t].len * (1 << (be.K[s] - 1)) * be.T[s] / 2);
+    }
+  }
+  // longest tiles first for the dynamic tile queue
+  std::vector<size_t> order(tiles.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return tile_cost[x] > tile_cost[y]; });
+  std::vector<BatchTile> sorted(tiles.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
+
+  pbvd_batch* b = reuse;
+  if (!b) {
+    b = new (std::nothrow) pbvd_batch();
+    if (!b) return PBVD_ENOMEM;
+    std::memset(b, 0, sizeof(*b));
+  }
+  b->device = dev;
+  b->entry = entry;
+  b->cta = cta;
+  size_t smem = 0;
+  int gmax = 0;
+  for (int s = 0; s < kBatchSlots; ++s) {
+    const int groups = cta / be.T[s];
+    smem = std::max(smem, (size_t)groups * be.scratch_words[s] * 4);
+    gmax = std::max(gmax, groups);
+  }
+  b->smem = smem;
+  int rc = PBVD_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    if ((int)smem > reg.batch_smem_set[entry]) {
+      cudaError_t e = be.set_max_smem((int)smem);
+      if (e != cudaSuccess) return cuda_fail(e);
+      reg.batch_smem_set[entry] = (int)smem;
+    }
+  }
+  int per_sm = 0;
+  PBVD_CUDA(be.occupancy(&per_sm, cta, smem));
+  if (per_sm < 1) return PBVD_EUNSUPPORTED;
+  b->grid = std::max(1, std::min<int>(per_sm * c0->sm_count, (int)std::max<size_t>(sorted.size(), 1)));
+  const int64_t n_slots = (int64_t)b->grid * gmax;
+  // one record slot size for every code of the launch, so that the records
+  // of different codes in concurrently running CTAs never overlap
+  int rs_max = 0;
+  size_t jmax = 0;
+  for (int s = 0; s < kBatchSlots; ++s)
+    if (slot_ctx[s]) {
+      rs_max = std::max(rs_max, be.words_per_stage[s]);
+      jmax = std::max(jmax, (size_t)(slot_ctx[s]->D + slot_ctx[s]->L));
+    }
+  const size_t surv = jmax * (size_t)n_slots * rs_max * 4;
+  if ((rc = grow(&b->d_pairs, &b->pairs_cap, pairs.size())) != PBVD_OK) return rc;
+  if ((rc = grow(&b->d_tiles, &b->tiles_cap, sorted.size())) != PBVD_OK) return rc;
+  if (!b->d_counter) PBVD_CUDA(cudaMalloc(&b->d_counter, sizeof(int32_t)));
+  size_t surv_words_cap = b->surv_bytes / 4;
+  if ((rc = grow(&b->d_surv, &surv_words_cap, (surv + 3) / 4)) != PBVD_OK) return rc;
+  b->surv_bytes = surv_words_cap * 4;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!pairs.empty())
+    PBVD_CUDA(cudaMemcpyAsync(b->d_pairs, pairs.data(), pairs.size() * sizeof(BatchPair), cudaMemcpyHostToDevice, st));
+  if (!sorted.empty())
+    PBVD_CUDA(cudaMemcpyAsync(b->d_tiles, sorted.data(), sorted.size() * sizeof(BatchTile), cudaMemcpyHostToDevice,
+                              st));
+  // kernel arguments
+  BatchArgs& a = b->args;
+  std::memset(&a, 0, sizeof(a));
+  for (int s = 0; s < kBatchSlots; ++s) {
+    KArgs& k = a.code[s];
+    const pbvd_ctx* c = slot_ctx[s] ? slot_ctx[s] : c0;
+    k.D = c->D;
+    k.L = c->L;
+    k.punct_P = slot_ctx[s] ? c->P : 0;
+    k.punct_C = slot_ctx[s] ? c->punct_C : 0;
+    std::memcpy(k.punct_off, c->punct_off, sizeof(k.punct_off));
+    std::memcpy(k.punct_pre, c->punct_pre, sizeof(k.punct_pre));
+    k.surv = b->d_surv;
+    k.surv_pairs = n_slots;
+    k.surv_rs = rs_max;
+    k.smem_surv = 0;
+    k.one = 1u;
+  }
+  a.pairs = b->d_pairs;
+  a.tiles = b->d_tiles;
+  a.ntiles = (int32_t)sorted.size();
+  a.gmax = gmax;
+  a.counter = b->d_counter;
+  *out = b;
+  return PBVD_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* pbvd_strerror(int code) {
@@ -262,6 +496,7 @@ int pbvd_create(pbvd_ctx** out, int K, int R, const uint32_t* gens, const uint8_
 
 void pbvd_destroy(pbvd_ctx* c) {
   if (!c) return;
+  if (c->batch) pbvd_batch_destroy(c->batch);
   if (c->work) {
     cudaDeviceSynchronize();
     cudaFree(c->work);
@@ -327,6 +562,7 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   a.n_blocks = p.n_blocks;
   a.n_pairs = p.n_pairs;
   a.surv_pairs = p.n_pairs;
+  a.surv_rs = registry().entries[p.entry].words_per_stage;
   a.D = c->D;
   a.L = c->L;
   a.smem_surv = p.smem_surv;
@@ -348,8 +584,45 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
 
 int pbvd_decode_batch(const pbvd_batch_item* items, size_t n_items, void* stream) {
   if (!items && n_items) return PBVD_EINVAL;
-  (void)stream;
-  return PBVD_EUNSUPPORTED;
+  if (n_items == 0) return PBVD_OK;
+  if (!items[0].ctx) return PBVD_EINVAL;
+  pbvd_ctx* lead = items[0].ctx;
+  int rc = batch_build(items, n_items, stream, lead->batch ? lead->batch : nullptr, &lead->batch);
+  if (rc != PBVD_OK) return rc;
+  return pbvd_batch_run(lead->batch, stream);
+}
+
+int pbvd_batch_prepare(pbvd_batch** out, const pbvd_batch_item* items, size_t n_items, void* stream) {
+  if (!out || (!items && n_items) || n_items == 0) return PBVD_EINVAL;
+  *out = nullptr;
+  pbvd_batch* b = nullptr;
+  int rc = batch_build(items, n_items, stream, nullptr, &b);
+  if (rc != PBVD_OK) {
+    if (b) pbvd_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return PBVD_OK;
+}
+
+int pbvd_batch_run(pbvd_batch* b, void* stream) {
+  if (!b) return PBVD_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->args.ntiles == 0) return PBVD_OK;
+  PBVD_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st));
+  const BatchKernelEntry& be = registry().batch[b->entry];
+  PBVD_CUDA(be.launch(b->args, b->grid, b->cta, b->smem, st));
+  return PBVD_OK;
+}
+
+void pbvd_batch_destroy(pbvd_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->d_pairs) cudaFree(b->d_pairs);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->d_surv) cudaFree(b->d_surv);
+  delete b;
 }
 
 }  // extern "C"
@@ -440,6 +713,7 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   a.n_blocks = p.n_blocks;
   a.n_pairs = p.n_pairs;
   a.surv_pairs = p.n_pairs;
+  a.surv_rs = registry().entries[p.entry].words_per_stage;
   a.D = c->D;
   a.L = c->L;
   a.smem_surv = 0;

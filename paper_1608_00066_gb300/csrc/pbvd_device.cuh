@@ -428,14 +428,20 @@ __device__ __forceinline__ void reinit_lane(uint32_t (&pm)[Shape<C, T>::M], int 
   }
 }
 
-// Work item of one group: a pair of PBs of one stream.
-struct PairWork {
+// Source of one PB: its stream (soft values, output bytes, length) and its
+// index in that stream.
+struct PbSrc {
   const int8_t* llr;
-  const int8_t* llr_end;
+  const int8_t* llr_end;  // end of the readable soft values
   uint8_t* out;
-  int64_t n;       // stages of the stream
-  int64_t bA;      // first PB of the pair
-  bool hasB;       // second PB exists
+  int64_t n;              // stages of the stream
+  int64_t b;              // block index within the stream
+};
+
+// Work item of one group: a pair of PBs, possibly of different streams.
+struct PairWork {
+  PbSrc A, B;
+  bool hasB;              // second PB exists
 };
 
 // One period (P stages starting at lock-step index i0) of the forward pass.
@@ -581,7 +587,7 @@ __device__ __forceinline__ int tb_step(int& psi, int& lm, int x, const uint32_t*
 // Global address of survivor record j of the group.
 template <class C, int T>
 __device__ __forceinline__ const uint32_t* global_record(const KArgs& a, int64_t gslot, int j) {
-  return a.surv + ((int64_t)j * a.surv_pairs + gslot) * Shape<C, T>::RW;
+  return a.surv + ((int64_t)j * a.surv_pairs + gslot) * a.surv_rs;
 }
 
 // Walks records [lo, hs] of NCH chains (descending) and emits, for records
@@ -628,7 +634,7 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
   }
   // ring: chunk ch holds records hs - ch*KR - q, q < KR, in buffer ch % NBUF
   const int nchunk = (hs - lo) / KR + 1;
-  const int64_t stride = a.surv_pairs * (int64_t)RW;
+  const int64_t stride = a.surv_pairs * (int64_t)a.surv_rs;
   const uint32_t* src_next = global_record<C, T>(a, gslot, hs);
   int issued = 0;
   auto issue = [&]() {
@@ -761,8 +767,8 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   const unsigned gmask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(T - 1)));
   const int L = a.L;
 
-  PbRun gA = pb_run<R>(a, wk.llr, wk.out, wk.n, wk.bA);
-  PbRun gB = wk.hasB ? pb_run<R>(a, wk.llr, wk.out, wk.n, wk.bA + 1) : gA;
+  PbRun gA = pb_run<R>(a, wk.A.llr, wk.A.out, wk.A.n, wk.A.b);
+  PbRun gB = wk.hasB ? pb_run<R>(a, wk.B.llr, wk.B.out, wk.B.n, wk.B.b) : gA;
   if (!wk.hasB) gB.iend = -1;
   const int I = max(gA.iend, gB.iend) + 1;  // lock-step stages
   const int J = I - L;                      // survivor records (stages L..I-1)
@@ -772,8 +778,8 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   int8_t* raw = reinterpret_cast<int8_t*>(scratch + raw_offset_words<C, T>());
   const int nchunk = (I + CH - 1) / CH;
   // relative value index at byte 0 of raw buffers 0 / 1 of PB A / B
-  int cbA0 = stage_raw_chunk<R, CH>(a, gA, wk.llr, wk.llr_end, 0, raw, tau, T);
-  int cbB0 = stage_raw_chunk<R, CH>(a, gB, wk.llr, wk.llr_end, 0, raw + CB, tau, T);
+  int cbA0 = stage_raw_chunk<R, CH>(a, gA, wk.A.llr, wk.A.llr_end, 0, raw, tau, T);
+  int cbB0 = stage_raw_chunk<R, CH>(a, gB, wk.B.llr, wk.B.llr_end, 0, raw + CB, tau, T);
   int cbA1 = 0, cbB1 = 0;
   asm volatile("cp.async.commit_group;" ::: "memory");
 
@@ -793,11 +799,12 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   // periods [fast_lo, fast_hi] need no per-stage checks
   const int dmax = max(gA.delta, gB.delta);
   const int fast_lo = dmax + (dmax > 0 ? 1 : 0);
-  const bool fast_ok = wk.hasB && (PUNCT || R != 2 || ((reinterpret_cast<uintptr_t>(wk.llr) & 1) == 0));
+  const bool fast_ok = wk.hasB && (PUNCT || R != 2 || (((reinterpret_cast<uintptr_t>(wk.A.llr) |
+                                                            reinterpret_cast<uintptr_t>(wk.B.llr)) & 1) == 0));
   const int fast_hi = fast_ok ? min(gA.iend, gB.iend) - (P - 1) : -1;
 
-  const int64_t rec_stride = a.surv_pairs * (int64_t)RW;  // global: words per record row
-  uint32_t* gsv = a.surv + gslot * RW + tau * S::W;
+  const int64_t rec_stride = a.surv_pairs * (int64_t)a.surv_rs;  // global: words per record row
+  uint32_t* gsv = a.surv + gslot * a.surv_rs + tau * S::W;
   uint32_t* ssv = svs + tau * S::W;
 
   const PipeConsts pc = pipe_consts(a);
@@ -811,8 +818,9 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
       __syncwarp(gmask);
       if (c + 1 < nchunk) {
         const int nb = (c + 1) & 1;
-        const int na = stage_raw_chunk<R, CH>(a, gA, wk.llr, wk.llr_end, c + 1, raw + nb * 2 * CB, tau, T);
-        const int nbb = stage_raw_chunk<R, CH>(a, gB, wk.llr, wk.llr_end, c + 1, raw + nb * 2 * CB + CB, tau, T);
+        const int na = stage_raw_chunk<R, CH>(a, gA, wk.A.llr, wk.A.llr_end, c + 1, raw + nb * 2 * CB, tau, T);
+        const int nbb =
+            stage_raw_chunk<R, CH>(a, gB, wk.B.llr, wk.B.llr_end, c + 1, raw + nb * 2 * CB + CB, tau, T);
         if (nb) { cbA1 = na; cbB1 = nbb; } else { cbA0 = na; cbB0 = nbb; }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
@@ -894,11 +902,13 @@ __global__ void __launch_bounds__(256, 1) pbvd_decode_kernel(const KArgs a) {
   uint32_t* scratch = smem + gl * SW;
   uint32_t* svs = smem + groups_per_cta * SW + (int64_t)gl * a.smem_rec_words;
   PairWork wk;
-  wk.llr = a.llr;
-  wk.llr_end = a.llr + a.llr_count;
-  wk.out = a.out;
-  wk.n = a.n;
-  wk.bA = 2 * pair;
+  wk.A.llr = a.llr;
+  wk.A.llr_end = a.llr + a.llr_count;
+  wk.A.out = a.out;
+  wk.A.n = a.n;
+  wk.A.b = 2 * pair;
+  wk.B = wk.A;
+  wk.B.b = 2 * pair + 1;
   wk.hasB = (2 * pair + 1) < a.n_blocks;
   decode_pair<C, T, PUNCT>(a, wk, pair, scratch, svs);
 }

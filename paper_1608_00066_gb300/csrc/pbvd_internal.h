@@ -11,11 +11,13 @@ namespace pbvd {
 struct KArgs {
   const int8_t* llr;      // soft values as sent
   uint8_t* out;           // packed decoded bits
-  uint32_t* surv;         // global survivor records, [J][surv_pairs][T*W] words
+  uint32_t* surv;         // global survivor records, [J][surv_pairs][surv_rs] words
   int64_t n;              // stages of the stream
   int64_t n_blocks;       // ceil(n / D)
   int64_t n_pairs;        // ceil(n_blocks / 2)
   int64_t surv_pairs;     // pair slots per record row of surv
+  int32_t surv_rs;        // words per record slot (>= the code's T*W record)
+  int32_t pad_rs;
   int32_t D, L;
   int32_t smem_surv;      // 1: survivor records in shared memory
   int32_t smem_rec_words; // shared-memory record words per group (smem mode)
@@ -27,20 +29,33 @@ struct KArgs {
   int16_t punct_pre[33];      // values sent in the columns before col
 };
 
-// Batched work: one entry per pair of PBs.
+// Batched work: one entry per pair of PBs (each PB from its own frame).
 struct BatchPair {
-  const int8_t* llr;
-  uint8_t* out;
-  int64_t n;        // stages of the frame
-  int64_t bA;       // first PB of the pair
+  const int8_t* llr[2];
+  const int8_t* llr_end[2];
+  uint8_t* out[2];
+  int64_t n[2];       // stages of the frame
+  int64_t b[2];       // block index within the frame
   int32_t hasB;
-  int32_t code;     // index into the batch's code table
+  int32_t pad;
 };
 
-struct BatchCode {
-  int32_t D, L;
-  int32_t punct_P, punct_C;
-  int16_t punct_off[32 * 4];
+// A tile: consecutive pairs of one code slot, one pair per group of a CTA.
+struct BatchTile {
+  int32_t slot;       // code slot of the combined kernel
+  int32_t count;      // pairs in the tile
+  int64_t first;      // index of the first pair
+};
+
+constexpr int kBatchSlots = 3;
+
+struct BatchArgs {
+  KArgs code[kBatchSlots];  // per code slot: D, L, puncture tables, survivors
+  const BatchPair* pairs;
+  const BatchTile* tiles;
+  int32_t ntiles;
+  int32_t gmax;             // survivor slots per CTA
+  int32_t* counter;         // next tile to take (zeroed before the launch)
 };
 
 using LaunchFn = cudaError_t (*)(const KArgs& a, int grid, int cta, size_t smem, cudaStream_t s);
@@ -59,9 +74,25 @@ struct KernelEntry {
   AttrFn set_max_smem;
 };
 
+using BatchLaunchFn = cudaError_t (*)(const BatchArgs& a, int grid, int cta, size_t smem, cudaStream_t s);
+using BatchOccFn = cudaError_t (*)(int* blocks_per_sm, int cta, size_t smem);
+
+// The combined persistent kernel for mixed-code batches.
+struct BatchKernelEntry {
+  int K[kBatchSlots], R[kBatchSlots], T[kBatchSlots];
+  uint32_t gens[kBatchSlots][3];
+  bool punct[kBatchSlots];
+  int words_per_stage[kBatchSlots];
+  int scratch_words[kBatchSlots];
+  BatchLaunchFn launch;
+  AttrFn set_max_smem;
+  BatchOccFn occupancy;
+};
+
 // Registries filled by the instance files.
 int register_k7(KernelEntry* out, int cap);
 int register_k9(KernelEntry* out, int cap);
 int register_small(KernelEntry* out, int cap);
+int register_batch(BatchKernelEntry* out, int cap);
 
 }  // namespace pbvd

@@ -33,6 +33,7 @@ EXPORTS = (
     "pbvd_create", "pbvd_destroy", "pbvd_decode", "pbvd_llr_count", "pbvd_decode_batch",
     "pbvd_set_config", "pbvd_get_config", "pbvd_strerror", "pbvd_last_cuda_error",
     "pbvd_decode_noalloc", "pbvd_noalloc_max_survivor_bytes",
+    "pbvd_batch_prepare", "pbvd_batch_run", "pbvd_batch_destroy",
 )
 
 
@@ -98,6 +99,12 @@ def load(path: Optional[str] = None):
         lib.pbvd_decode_noalloc.restype = I
         lib.pbvd_noalloc_max_survivor_bytes.argtypes = []
         lib.pbvd_noalloc_max_survivor_bytes.restype = SZ
+        lib.pbvd_batch_prepare.argtypes = [ctypes.POINTER(V), V, SZ, V]
+        lib.pbvd_batch_prepare.restype = I
+        lib.pbvd_batch_run.argtypes = [V, V]
+        lib.pbvd_batch_run.restype = I
+        lib.pbvd_batch_destroy.argtypes = [V]
+        lib.pbvd_batch_destroy.restype = None
         _lib = lib
         return lib
 
@@ -155,11 +162,34 @@ def pbvd_llr_count(ctx: int, n_stages: int) -> int:
 
 def pbvd_decode_batch(items: Sequence[tuple], stream: int = 0) -> None:
     """items: sequence of (ctx, d_llr, n_stages, d_out)."""
+    arr = _items(items)
+    _check(load().pbvd_decode_batch(ctypes.cast(arr, ctypes.c_void_p), len(items), stream or None),
+           "pbvd_decode_batch")
+
+
+def _items(items):
     arr = (pbvd_batch_item * max(len(items), 1))()
     for i, (ctx, llr, n, out) in enumerate(items):
         arr[i].ctx, arr[i].d_llr, arr[i].n_stages, arr[i].d_out = ctx, llr, n, out
-    _check(load().pbvd_decode_batch(ctypes.cast(arr, ctypes.c_void_p), len(items), stream or None),
-           "pbvd_decode_batch")
+    return arr
+
+
+def pbvd_batch_prepare(items: Sequence[tuple], stream: int = 0) -> int:
+    """Builds the work list of items (ctx, d_llr, n_stages, d_out); returns a
+    batch handle for pbvd_batch_run / pbvd_batch_destroy."""
+    arr = _items(items)
+    h = ctypes.c_void_p()
+    _check(load().pbvd_batch_prepare(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                     stream or None), "pbvd_batch_prepare")
+    return h.value
+
+
+def pbvd_batch_run(batch: int, stream: int = 0) -> None:
+    _check(load().pbvd_batch_run(batch, stream or None), "pbvd_batch_run")
+
+
+def pbvd_batch_destroy(batch: int) -> None:
+    load().pbvd_batch_destroy(batch)
 
 
 def pbvd_set_config(ctx: int, threads_per_pair: int = 0, cta_threads: int = 0,

@@ -154,3 +154,22 @@ def test_full_size_stream_sampled(name, ebn0, D, L, seed):
         assert np.array_equal(got[o0:o1], want[o0:o1]), b
     ber = float((got[:k] != f.msg).mean())
     assert ber < 1e-3, ber
+
+
+def test_unaligned_soft_values():
+    """Soft values starting at an odd address (no 2-byte loads) decode the
+    same bits."""
+    spec = synth.K7_R12
+    f = synth.make_frame(spec, 30000, 1.5, seed=14)
+    n = f.n_stages
+    want = oracle_bits(spec, f.llr, n, 256, 42)
+    dec = make_decoder(spec, 256, 42)
+    big = torch.zeros(len(f.llr) + 1, dtype=torch.int8, device="cuda")
+    big[1:] = torch.from_numpy(f.llr).cuda()
+    view = big[1:]
+    assert view.data_ptr() % 2 == 1
+    for T in (1, 2, 4):
+        dec.set_config(threads_per_pair=T)
+        out = dec.decode(view, n)
+        torch.cuda.synchronize()
+        assert np.array_equal(np.unpackbits(out.cpu().numpy(), bitorder="little")[:n], want), T
