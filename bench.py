@@ -59,29 +59,62 @@ def peak_int16_ops(sm_count: int = 152, clock_hz: float = 2.07e9) -> float:
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons during a region."""
+    """Samples SM clock, max clock and clock-event reasons of one GPU during a
+    region: NVML through ctypes every ~2 ms, else nvidia-smi every 200 ms."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index: int = 0):
         self.index = index
-        self.samples = []
+        self.samples = []  # (sm_mhz, max_mhz, reason_bits or names)
         self._stop = threading.Event()
         self._thr = None
+        self._nvml = None
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                if lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(h)) == 0:
+                    self._nvml = (lib, h)
+        except Exception:
+            self._nvml = None
+
+    def _sample_nvml(self):
+        import ctypes
+        lib, h = self._nvml
+        cur, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(cur))
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        fn(h, ctypes.byref(rs))
+        names = [v for k, v in self.REASONS.items() if rs.value & k]
+        self.samples.append((float(cur.value), float(mx.value), names))
+
+    def _sample_smi(self):
+        out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,"
+                              "clocks_event_reasons.sw_power_cap,clocks_event_reasons.hw_slowdown,"
+                              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.hw_thermal_slowdown",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5).stdout
+        f = [x.strip() for x in out.strip().split(",")]
+        if len(f) >= 6 and f[0].replace(".", "").isdigit():
+            names = [n for n, v in zip(("sw_power_cap", "hw_slowdown", "sw_thermal_slowdown",
+                                        "hw_thermal_slowdown"), f[2:6]) if v.lower() == "active"]
+            self.samples.append((float(f[0]), float(f[1]), names))
 
     def _run(self):
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
+                if self._nvml:
+                    self._sample_nvml()
+                    self._stop.wait(0.002)
+                else:
+                    self._sample_smi()
+                    self._stop.wait(0.2)
             except Exception:
-                pass
-            self._stop.wait(0.2)
+                self._stop.wait(0.2)
 
     def __enter__(self):
         self._thr = threading.Thread(target=self._run, daemon=True)
@@ -95,15 +128,11 @@ class ClockSampler:
 
     def summary(self):
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
-                          if len(s) > 4 + i and s[4 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock samples"], "samples": 0}
+        sm = [x[0] for x in self.samples]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.samples),
+                "reasons": sorted({r for x in self.samples for r in x[2]}), "samples": len(self.samples),
+                "source": "nvml" if self._nvml else "nvidia-smi"}
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -178,12 +207,14 @@ def run_ours(args, rank: int, world: int):
     frame = synth.make_frame(spec, K_INFO, EBN0_DB, seed=SEED + rank)
     n = frame.n_stages
     dec = pbvd.Decoder(spec.K, spec.gens, None, D_BLOCK, L_OVERLAP)
-    if args.tune:
-        dec.set_config(**json.loads(args.tune))
-    cfg = dec.get_config(n)
     d_llr = torch.from_numpy(frame.llr).cuda()
     nbytes = (n + 7) // 8
     d_out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    if args.tune:
+        dec.set_config(**json.loads(args.tune))
+    else:
+        dec.autotune(d_llr, n, d_out, reps=3)  # kernel configuration, outside the timed region
+    cfg = dec.get_config(n)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (~129 MB)
     stream = torch.cuda.current_stream()
 
@@ -240,6 +271,9 @@ def run_ours(args, rank: int, world: int):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms, e2e_ms = float(t[0]), float(t[1])
 
+    batched = run_batched(args) if (rank == 0 and not args.no_batch) else None
+    latency = run_latency(args) if (rank == 0 and not args.no_batch) else None
+
     value = K_INFO * world / (ms * 1e-3) / 1e9
     e2e = K_INFO * world / (e2e_ms * 1e-3) / 1e9
     ops = algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP) * K_INFO
@@ -262,20 +296,107 @@ def run_ours(args, rank: int, world: int):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "ber": ber,
+        "batched_vs_plain": batched,
+        "latency": latency,
         "paper_context": PAPER_CONTEXT,
     }
     return result, frame
 
 
+def run_batched(args):
+    """Batched workload: 10,000 terminated frames, info lengths uniform in
+    [40, 6144], code drawn per frame from K=7 r1/2, K=7 r3/4 ([110;101]) and
+    K=9 r1/3, Eb/N0 uniform in [1, 5] dB.  D per code is tuned (L = 42 for
+    K=7, 64 for K=9); the batch is one persistent launch replayed from a CUDA
+    graph; plain = one pbvd_decode launch per frame with the same (D, L), so
+    the same bits."""
+    import torch
+    from paper_1608_00066_gb300 import pbvd, synth, tune
+    frames = synth.batch_frames(10000, seed=4001)
+    bits = int(sum(len(f.msg) for f in frames))
+    flat = np.concatenate([f.llr for f in frames])
+    d_all = torch.from_numpy(flat).cuda()
+    outs = torch.zeros(sum((f.n_stages + 7) // 8 for f in frames), dtype=torch.uint8, device="cuda")
+    lp, op, off, ooff = [], [], 0, 0
+    for f in frames:
+        lp.append(d_all.data_ptr() + off)
+        op.append(outs.data_ptr() + ooff)
+        off += len(f.llr)
+        ooff += (f.n_stages + 7) // 8
+    choice, _, _ = tune.tune_batch_geometry(frames, lp, op, candidates=(512, 1024, 2048, 4096), reps=2)
+    decs = {nm: pbvd.Decoder(synth.CODES[nm].K, synth.CODES[nm].gens, synth.CODES[nm].puncture, *choice[nm])
+            for nm in choice}
+    items = tune.make_items(frames, decs, lp, op)
+    b = pbvd.pbvd_batch_prepare(items)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pbvd.pbvd_batch_run(b, s.cuda_stream)
+    for _ in range(max(3, args.warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(5, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms_b = statistics.median(ts)
+    ref = outs.clone()
+    for it in items[:200]:
+        pbvd.pbvd_decode(*it)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for it in items:
+        pbvd.pbvd_decode(*it)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    same = bool(torch.equal(ref, outs))
+    pbvd.pbvd_batch_destroy(b)
+    return {"workload": "10,000 mixed-code frames (K7 r1/2, K7 r3/4, K9 r1/3), k ~ U[40,6144], Eb/N0 ~ U[1,5] dB",
+            "info_bits": bits, "geometry": {k: list(v) for k, v in choice.items()},
+            "batched_gbps": round(bits / ms_b / 1e6, 3), "batched_ms": round(ms_b, 4),
+            "plain_gbps": round(bits / ms_p / 1e6, 4), "plain_ms": round(ms_p, 2),
+            "plain_launches": len(items), "identical_bits": same}
+
+
+def run_latency(args):
+    """One 4096-bit K=7 r1/2 frame at 3 dB, D=512, L=42: device time of one
+    decode (median over repetitions), tuned kernel configuration."""
+    import torch
+    from paper_1608_00066_gb300 import pbvd, synth
+    f = synth.make_frame(synth.K7_R12, 4096, 3.0, seed=1001)
+    dec = pbvd.Decoder(7, synth.K7_R12.gens, None, 512, 42)
+    d = torch.from_numpy(f.llr).cuda()
+    o = torch.empty((f.n_stages + 7) // 8, dtype=torch.uint8, device="cuda")
+    cfg, _ = dec.autotune(d, f.n_stages, o, reps=5)
+    ts = []
+    for _ in range(50):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dec.decode(d, f.n_stages, o)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    return {"workload": "one K7 r1/2 frame, 4096 info bits, D=512 L=42", "kernel_config": cfg,
+            "p50_us": round(1000 * ts[len(ts) // 2], 1), "p99_us": round(1000 * ts[int(len(ts) * 0.99) - 1], 1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tune", default="", help="JSON kernel config (threads_per_pair, cta_threads, ...)")
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and latency extras")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

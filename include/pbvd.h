@@ -161,6 +161,15 @@ PBVD_API int pbvd_set_config(pbvd_ctx *ctx, const pbvd_config *cfg);
 /* Reads back the configuration pbvd_decode would use for n_stages. */
 PBVD_API int pbvd_get_config(const pbvd_ctx *ctx, size_t n_stages, pbvd_config *cfg);
 
+/* Autotuner (not in the paper): decodes the caller's data with every built
+ * threads-per-pair value, CTA size and survivor placement, timing each with
+ * CUDA events on stream (reps timed runs after one warm-up; synchronises),
+ * and keeps the fastest configuration in ctx (also written to best / best_ms
+ * when non-NULL).  The decoded bits do not depend on the configuration.  D and
+ * L, which do change the bits, are context parameters and are not tuned here. */
+PBVD_API int pbvd_autotune(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages, uint8_t *d_out,
+                           void *stream, int reps, pbvd_config *best, float *best_ms);
+
 /* Allocation-free variant of pbvd_decode (no counterpart in the paper).
  * For callers that must not allocate device memory while decoding: code
  * running under CUDA stream capture, real-time receive chains that reserve

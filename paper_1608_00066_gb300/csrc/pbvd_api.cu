@@ -736,3 +736,69 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
 size_t pbvd_noalloc_max_survivor_bytes(void) { return kNoAllocSurvivorBytes; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- tuning --
+
+extern "C" {
+
+int pbvd_autotune(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_out, void* stream, int reps,
+                  pbvd_config* best_cfg, float* best_ms) {
+  if (!c || !d_llr || !d_out || n_stages == 0) return PBVD_EINVAL;
+  if (reps < 1) reps = 3;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const pbvd_config saved = c->cfg;
+  cudaEvent_t e0, e1;
+  PBVD_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce);
+  }
+  pbvd_config best = saved;
+  float best_t = -1.0f;
+  int rc = PBVD_OK;
+  for (int T = 1; T <= 32 && rc == PBVD_OK; T *= 2) {
+    if (find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) continue;
+    for (int cta : {32, 64, 128, 256}) {
+      if (cta % T) continue;
+      for (int smem = 0; smem <= 1; ++smem) {
+        c->cfg.threads_per_pair = T;
+        c->cfg.cta_threads = cta;
+        c->cfg.survivors_in_smem = smem;
+        Plan p;
+        if (plan_decode(c, n_stages, &p) != PBVD_OK) continue;
+        // skip shapes that cannot fill the GPU with one pair per group
+        if (smem && p.n_pairs > 4 * c->sm_count) continue;
+        if (pbvd_decode(c, d_llr, n_stages, d_out, stream) != PBVD_OK) continue;  // warm-up
+        float tot = 0.0f;
+        for (int r = 0; r < reps && rc == PBVD_OK; ++r) {
+          cudaEventRecord(e0, st);
+          rc = pbvd_decode(c, d_llr, n_stages, d_out, stream);
+          cudaEventRecord(e1, st);
+          ce = cudaEventSynchronize(e1);
+          if (ce != cudaSuccess) rc = cuda_fail(ce);
+          float ms = 0.0f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          tot += ms;
+        }
+        const float t = tot / reps;
+        if (rc == PBVD_OK && (best_t < 0.0f || t < best_t)) {
+          best_t = t;
+          best = c->cfg;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PBVD_OK || best_t < 0.0f) {
+    c->cfg = saved;
+    return rc != PBVD_OK ? rc : PBVD_EUNSUPPORTED;
+  }
+  c->cfg = best;
+  if (best_cfg) *best_cfg = best;
+  if (best_ms) *best_ms = best_t;
+  return PBVD_OK;
+}
+
+}  // extern "C"

@@ -33,7 +33,7 @@ EXPORTS = (
     "pbvd_create", "pbvd_destroy", "pbvd_decode", "pbvd_llr_count", "pbvd_decode_batch",
     "pbvd_set_config", "pbvd_get_config", "pbvd_strerror", "pbvd_last_cuda_error",
     "pbvd_decode_noalloc", "pbvd_noalloc_max_survivor_bytes",
-    "pbvd_batch_prepare", "pbvd_batch_run", "pbvd_batch_destroy",
+    "pbvd_batch_prepare", "pbvd_batch_run", "pbvd_batch_destroy", "pbvd_autotune",
 )
 
 
@@ -105,6 +105,9 @@ def load(path: Optional[str] = None):
         lib.pbvd_batch_run.restype = I
         lib.pbvd_batch_destroy.argtypes = [V]
         lib.pbvd_batch_destroy.restype = None
+        lib.pbvd_autotune.argtypes = [V, V, SZ, V, V, I, ctypes.POINTER(pbvd_config),
+                                      ctypes.POINTER(ctypes.c_float)]
+        lib.pbvd_autotune.restype = I
         _lib = lib
         return lib
 
@@ -205,6 +208,17 @@ def pbvd_get_config(ctx: int, n_stages: int) -> dict:
             "survivors_in_smem": cfg.survivors_in_smem}
 
 
+def pbvd_autotune(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0, reps: int = 3):
+    """Times the built kernel configurations on this data and keeps the
+    fastest in ctx; returns (config dict, milliseconds)."""
+    cfg = pbvd_config()
+    ms = ctypes.c_float()
+    _check(load().pbvd_autotune(ctx, d_llr, n_stages, d_out, stream or None, reps, ctypes.byref(cfg),
+                                ctypes.byref(ms)), "pbvd_autotune")
+    return ({"threads_per_pair": cfg.threads_per_pair, "cta_threads": cfg.cta_threads,
+             "survivors_in_smem": cfg.survivors_in_smem}, float(ms.value))
+
+
 def pbvd_strerror(code: int) -> str:
     return load().pbvd_strerror(code).decode()
 
@@ -237,6 +251,15 @@ class Decoder:
 
     def get_config(self, n_stages: int) -> dict:
         return pbvd_get_config(self.ctx, n_stages)
+
+    def autotune(self, llr, n_stages: int, out=None, reps: int = 3):
+        """Tunes the kernel configuration on this input (torch tensors)."""
+        import torch
+        nbytes = (n_stages + 7) // 8
+        if out is None:
+            out = torch.empty(nbytes, dtype=torch.uint8, device=llr.device)
+        s = torch.cuda.current_stream(llr.device)
+        return pbvd_autotune(self.ctx, llr.data_ptr(), n_stages, out.data_ptr(), s.cuda_stream, reps)
 
     def decode(self, llr, n_stages: int, out=None, stream=None):
         """llr: int8 CUDA tensor of the sent soft values; returns (or fills) a
