@@ -191,6 +191,28 @@ def cpu_oracle_rate(llr: np.ndarray, n: int, target_s: float = 15.0, max_cores=N
 
 # -------------------------------------------------------------- our arm
 
+def max_over_ranks(values, world: int, device="cuda"):
+    """Per-rank timings (ms) -> their maximum over all ranks (every rank gets
+    the same list).  No-op on one rank."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def aggregate_gbps(info_bits_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the bits all ranks decoded / the slowest rank's time."""
+    return info_bits_per_rank * world / (ms * 1e-3) / 1e9
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank decodes its own stream (weak scaling)."""
+    return SEED + rank
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_1608_00066_gb300 import build as pbuild
@@ -204,7 +226,7 @@ def run_ours(args, rank: int, world: int):
         import torch.distributed as dist
         dist.barrier()
     spec = synth.K7_R12
-    frame = synth.make_frame(spec, K_INFO, EBN0_DB, seed=SEED + rank)
+    frame = synth.make_frame(spec, K_INFO, EBN0_DB, seed=rank_seed(rank))
     n = frame.n_stages
     dec = pbvd.Decoder(spec.K, spec.gens, None, D_BLOCK, L_OVERLAP)
     d_llr = torch.from_numpy(frame.llr).cuda()
@@ -265,17 +287,13 @@ def run_ours(args, rank: int, world: int):
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], world)
 
     batched = run_batched(args) if (rank == 0 and not args.no_batch) else None
     latency = run_latency(args) if (rank == 0 and not args.no_batch) else None
 
-    value = K_INFO * world / (ms * 1e-3) / 1e9
-    e2e = K_INFO * world / (e2e_ms * 1e-3) / 1e9
+    value = aggregate_gbps(K_INFO, world, ms)
+    e2e = aggregate_gbps(K_INFO, world, e2e_ms)
     ops = algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP) * K_INFO
     peak = peak_int16_ops()
     achieved = ops / (ms * 1e-3)
@@ -387,6 +405,48 @@ def run_latency(args):
             "p50_us": round(1000 * ts[len(ts) // 2], 1), "p99_us": round(1000 * ts[int(len(ts) * 0.99) - 1], 1)}
 
 
+SERVE_RATES = (0.5e6, 1.0e6, 2.0e6, 4.0e6)   # offered frames/s
+SERVE_WINDOW_S = 0.25
+
+
+def run_serving(args):
+    """Serving: Poisson frame arrivals (k log-uniform in [100, 100000], code
+    uniform over K7 r1/2, K7 r3/4, K9 r1/3, Eb/N0 uniform in [1, 5] dB)
+    served by continuous batching from pinned host memory (H2D, batched
+    decode, D2H inside the measured latency), plus 64 continuous K7 r1/2
+    streams pushed in 4096-stage chunks every 2 ms.  Each offered rate runs a
+    0.25 s arrival window; 0.25 M frames/s is the 0.5 M/s process thinned by
+    half (below saturation)."""
+    import torch
+    from paper_1608_00066_gb300 import serve, synth
+    pool = serve.build_request_pool(1024, seed=5001)
+    cfg = serve.ServeConfig()
+    srv = serve.Server(pool, cfg)
+    # warm-up: one short run
+    srv.run(serve.poisson_arrivals(1e5, 0.01, seed=5000))
+    points = []
+    base = serve.poisson_arrivals(SERVE_RATES[0], SERVE_WINDOW_S, seed=5001)
+    runs = [("0.25M/s (0.5M/s thinned by 1/2)", serve.thin(base, 0.5, seed=5002))]
+    runs += [("%gM/s" % (r / 1e6), base if r == SERVE_RATES[0] else
+              serve.poisson_arrivals(r, SERVE_WINDOW_S, seed=5001 + int(r / 1e5))) for r in SERVE_RATES]
+    for label, arr in runs:
+        feeder = serve.StreamFeeder(srv.decoders["K7_r1/2"], synth.K7_R12, n_streams=64, chunk=4096, period=2e-3,
+                                    n_chunks=int(SERVE_WINDOW_S / 2e-3), seed=5003)
+        res = srv.run(arr, feeder)
+        res["offered"] = label
+        points.append(res)
+        feeder.destroy()
+        torch.cuda.synchronize()
+    srv.close()
+    return {"workload": "Poisson frame requests, k log-uniform [100, 100000], mixed codes; "
+                        "64 K7 r1/2 streams x 4096 stages / 2 ms",
+            "config": {"arena_bytes": cfg.arena_bytes, "inflight": cfg.inflight,
+                       "max_batch_bits": cfg.max_batch_bits, "max_wait_ms": cfg.max_wait_ms,
+                       "geometry": {k: list(v) for k, v in cfg.geometry.items()}, "window_s": SERVE_WINDOW_S,
+                       "latency": "host clock from arrival to completion of the D2H copy"},
+            "points": points}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,6 +457,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and latency extras")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -411,6 +472,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     result, frame = run_ours(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_serve:
+        result["serving"] = run_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_oracle_rate(frame.llr, frame.n_stages)
     if rank == 0:

@@ -136,6 +136,16 @@ typedef struct pbvd_batch pbvd_batch;
 PBVD_API int pbvd_batch_prepare(pbvd_batch **out, const pbvd_batch_item *items, size_t n_items,
                                 void *stream);
 
+/* Replaces the items of a prepared batch, reusing its device buffers (they
+ * grow, with a device synchronisation, only when the new work list is larger
+ * than any before).  The upload is ordered on stream, so a previous run of
+ * the batch must be on the same stream.  reserve_sms > 0 sizes the
+ * persistent grid for that many SMs fewer (leaving room for other work, e.g.
+ * stream pushes); 0 = fill the GPU.  For serving loops that decode a new set
+ * of frames every iteration. */
+PBVD_API int pbvd_batch_update(pbvd_batch *batch, const pbvd_batch_item *items, size_t n_items,
+                               int reserve_sms, void *stream);
+
 /* Decodes a prepared batch: resets the tile queue and launches the kernel. */
 PBVD_API int pbvd_batch_run(pbvd_batch *batch, void *stream);
 
@@ -194,6 +204,45 @@ PBVD_API int pbvd_decode_noalloc(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_st
 
 /* Size of the fixed survivor array of pbvd_decode_noalloc, in bytes. */
 PBVD_API size_t pbvd_noalloc_max_survivor_bytes(void);
+
+/* Continuous streams with device-resident path metrics (serving; the paper
+ * decodes blocks only).  A stream of an unpunctured K=7 (171,133) or K=9
+ * (557,663,711) code is decoded by Eq. (1) run once over all its stages with
+ * the metrics carried in device memory between pushes; segment m of D stages
+ * is released, once stage (m+1)D + L - 1 exists, by traceback from S_0 at that
+ * stage; closing the stream (whose last v stages must be the zero tail)
+ * releases the rest by traceback from S_0 at the last stage.  Bit s of the
+ * stream goes to bit s & 7 of byte s >> 3 of d_out (device, caller-owned,
+ * out_capacity stages).  Pushes are ordered on the CUDA stream given; a
+ * stream object must not be pushed from two host threads at once. */
+typedef struct pbvd_stream pbvd_stream;
+
+/* Opens a stream on ctx accepting up to max_push stages per push; allocates
+ * its device state (metrics, a survivor ring of max_push + D + L + 2P
+ * records, a staging buffer). */
+PBVD_API int pbvd_stream_open(pbvd_stream **out, pbvd_ctx *ctx, size_t max_push, uint8_t *d_out,
+                              size_t out_capacity);
+
+/* Appends n_stages stages (device soft values, R per stage) and decodes them. */
+PBVD_API int pbvd_stream_push(pbvd_stream *s, const int8_t *d_llr, size_t n_stages, void *stream);
+
+/* Pushes to count distinct streams of the same code, one kernel launch per
+ * 128 streams; n_stages[i] may be 0, and d_llr and n_stages may both be NULL
+ * when no stream receives stages.  With close != 0 every stream is closed
+ * after its push.  A push decodes whole periods of P stages (P = 3 for K=7,
+ * 4 for K=9 streams); the rest waits in the stream's carry buffer. */
+PBVD_API int pbvd_stream_push_many(pbvd_stream *const *s, const int8_t *const *d_llr,
+                                   const size_t *n_stages, size_t count, int close, void *stream);
+
+/* Closes the stream: decodes what is left and releases every bit. */
+PBVD_API int pbvd_stream_close(pbvd_stream *s, void *stream);
+
+/* Number of leading stages whose bits are final in d_out once the pushes so
+ * far have completed on their CUDA stream. */
+PBVD_API int64_t pbvd_stream_released(const pbvd_stream *s);
+
+/* Frees the stream's device state (synchronises the device first). */
+PBVD_API void pbvd_stream_destroy(pbvd_stream *s);
 
 /* Message for an error code (static string). */
 PBVD_API const char *pbvd_strerror(int code);

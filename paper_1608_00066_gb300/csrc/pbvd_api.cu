@@ -37,6 +37,7 @@ struct Registry {
   std::vector<int> smem_set;  // max dynamic smem already granted per entry
   std::vector<BatchKernelEntry> batch;
   std::vector<int> batch_smem_set;
+  std::vector<StreamKernelEntry> stream;
 };
 
 Registry& registry() {
@@ -54,6 +55,9 @@ Registry& registry() {
     const int nb = register_batch(bb, 4);
     reg.batch.assign(bb, bb + nb);
     reg.batch_smem_set.assign(nb, 48 * 1024);
+    StreamKernelEntry sb[8];
+    const int ns = register_stream(sb, 8);
+    reg.stream.assign(sb, sb + ns);
   });
   return reg;
 }
@@ -244,7 +248,8 @@ int grow(T** p, size_t* cap, size_t need) {
 // frame grouped by code slot, sorted by forward length and paired, cut into
 // tiles of one CTA's pairs, tiles ordered longest first.  Uploads it on
 // 'stream'.
-int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd_batch* reuse, pbvd_batch** out) {
+int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd_batch* reuse, int reserve_sms,
+                pbvd_batch** out) {
   Registry& reg = registry();
   if (reg.batch.empty()) return PBVD_EUNSUPPORTED;
   const int entry = 0;
@@ -362,7 +367,8 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
   int per_sm = 0;
   PBVD_CUDA(be.occupancy(&per_sm, cta, smem));
   if (per_sm < 1) return PBVD_EUNSUPPORTED;
-  b->grid = std::max(1, std::min<int>(per_sm * c0->sm_count, (int)std::max<size_t>(sorted.size(), 1)));
+  const int grid_cap = per_sm * std::max(1, c0->sm_count - reserve_sms);
+  b->grid = std::max(1, std::min<int>(grid_cap, (int)std::max<size_t>(sorted.size(), 1)));
   const int64_t n_slots = (int64_t)b->grid * gmax;
   // one record slot size for every code of the launch, so that the records
   // of different codes in concurrently running CTAs never overlap
@@ -587,7 +593,7 @@ int pbvd_decode_batch(const pbvd_batch_item* items, size_t n_items, void* stream
   if (n_items == 0) return PBVD_OK;
   if (!items[0].ctx) return PBVD_EINVAL;
   pbvd_ctx* lead = items[0].ctx;
-  int rc = batch_build(items, n_items, stream, lead->batch ? lead->batch : nullptr, &lead->batch);
+  int rc = batch_build(items, n_items, stream, lead->batch ? lead->batch : nullptr, 0, &lead->batch);
   if (rc != PBVD_OK) return rc;
   return pbvd_batch_run(lead->batch, stream);
 }
@@ -596,13 +602,19 @@ int pbvd_batch_prepare(pbvd_batch** out, const pbvd_batch_item* items, size_t n_
   if (!out || (!items && n_items) || n_items == 0) return PBVD_EINVAL;
   *out = nullptr;
   pbvd_batch* b = nullptr;
-  int rc = batch_build(items, n_items, stream, nullptr, &b);
+  int rc = batch_build(items, n_items, stream, nullptr, 0, &b);
   if (rc != PBVD_OK) {
     if (b) pbvd_batch_destroy(b);
     return rc;
   }
   *out = b;
   return PBVD_OK;
+}
+
+int pbvd_batch_update(pbvd_batch* b, const pbvd_batch_item* items, size_t n_items, int reserve_sms, void* stream) {
+  if (!b || !items || n_items == 0 || reserve_sms < 0) return PBVD_EINVAL;
+  pbvd_batch* same = b;
+  return batch_build(items, n_items, stream, b, reserve_sms, &same);
 }
 
 int pbvd_batch_run(pbvd_batch* b, void* stream) {
@@ -799,6 +811,156 @@ int pbvd_autotune(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_
   if (best_cfg) *best_cfg = best;
   if (best_ms) *best_ms = best_t;
   return PBVD_OK;
+}
+
+}  // extern "C"
+
+// -------------------------------------------------------------- streams --
+
+struct pbvd_stream {
+  pbvd_ctx* ctx;
+  int entry;
+  int P, R, H;
+  size_t max_push;
+  int64_t t;          // stages decoded (forward)
+  int64_t released;   // stages whose bits are final
+  int carry;          // stages held back (< P)
+  int closed;
+  uint8_t* d_out;
+  size_t out_cap;     // stages
+  uint32_t* d_pm;
+  uint32_t* d_ring;
+  int8_t* d_carry;
+};
+
+namespace {
+
+int find_stream_entry(const pbvd_ctx* c) {
+  Registry& reg = registry();
+  for (size_t i = 0; i < reg.stream.size(); ++i) {
+    const StreamKernelEntry& e = reg.stream[i];
+    if (e.K != c->K || e.R != c->R) continue;
+    bool same = true;
+    for (int r = 0; r < c->R; ++r) same = same && e.gens[r] == c->gens[r];
+    if (same) return (int)i;
+  }
+  return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbvd_stream_open(pbvd_stream** out, pbvd_ctx* c, size_t max_push, uint8_t* d_out, size_t out_capacity) {
+  if (!out) return PBVD_EINVAL;
+  *out = nullptr;
+  if (!c || !d_out || max_push == 0 || max_push > ((size_t)1 << 24) || out_capacity == 0) return PBVD_EINVAL;
+  if (c->P) return PBVD_EUNSUPPORTED;
+  const int entry = find_stream_entry(c);
+  if (entry < 0) return PBVD_EUNSUPPORTED;
+  const StreamKernelEntry& e = registry().stream[entry];
+  pbvd_stream* s = new (std::nothrow) pbvd_stream();
+  if (!s) return PBVD_ENOMEM;
+  std::memset(s, 0, sizeof(*s));
+  s->ctx = c;
+  s->entry = entry;
+  s->P = e.P;
+  s->R = c->R;
+  s->max_push = max_push;
+  // records of the oldest unreleased stage up to the last stage of a push
+  s->H = (int)(max_push + c->D + c->L + 2 * e.P);
+  s->d_out = d_out;
+  s->out_cap = out_capacity;
+  // known start: S_0 at 0, every other state at 8192 (lane A)
+  std::vector<uint32_t> pm0(c->N, 8192u);
+  pm0[0] = 0u;
+  cudaError_t ce = cudaMalloc(&s->d_pm, sizeof(uint32_t) * c->N);
+  if (ce == cudaSuccess) ce = cudaMalloc(&s->d_ring, (size_t)s->H * e.words_per_stage * sizeof(uint32_t));
+  if (ce == cudaSuccess) ce = cudaMalloc(&s->d_carry, (size_t)e.P * c->R);
+  if (ce == cudaSuccess) ce = cudaMemcpy(s->d_pm, pm0.data(), sizeof(uint32_t) * c->N, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    pbvd_stream_destroy(s);
+    return cuda_fail(ce);
+  }
+  *out = s;
+  return PBVD_OK;
+}
+
+void pbvd_stream_destroy(pbvd_stream* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  if (s->d_pm) cudaFree(s->d_pm);
+  if (s->d_ring) cudaFree(s->d_ring);
+  if (s->d_carry) cudaFree(s->d_carry);
+  delete s;
+}
+
+int64_t pbvd_stream_released(const pbvd_stream* s) { return s ? s->released : -1; }
+
+int pbvd_stream_push_many(pbvd_stream* const* ss, const int8_t* const* d_llr, const size_t* n_stages,
+                          size_t count, int close, void* stream) {
+  if (!ss || count == 0) return PBVD_EINVAL;
+  const int entry = ss[0] ? ss[0]->entry : -1;
+  for (size_t i = 0; i < count; ++i) {
+    const pbvd_stream* s = ss[i];
+    if (!s || s->closed || s->entry != entry) return PBVD_EINVAL;
+    for (size_t j = 0; j < i; ++j)
+      if (ss[j] == s) return PBVD_EINVAL;
+    const size_t n = n_stages ? n_stages[i] : 0;
+    if (n > s->max_push || (n && (!d_llr || !d_llr[i]))) return PBVD_EINVAL;
+    if ((size_t)(s->t + s->carry) + n > s->out_cap) return PBVD_EINVAL;
+  }
+  const StreamKernelEntry& e = registry().stream[entry];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  static thread_local StreamLaunch p;
+  for (size_t base = 0; base < count; base += kStreamsPerLaunch) {
+    const int m = (int)std::min<size_t>(kStreamsPerLaunch, count - base);
+    p.count = m;
+    p.one = 1u;
+    for (int i = 0; i < m; ++i) {
+      const pbvd_stream* s = ss[base + i];
+      const size_t n = n_stages ? n_stages[base + i] : 0;
+      StreamDev& d = p.d[i];
+      d.pm = s->d_pm;
+      d.ring = s->d_ring;
+      d.carry = s->d_carry;
+      d.llr = n ? d_llr[base + i] : nullptr;
+      d.out = s->d_out;
+      d.t0 = s->t;
+      d.released = s->released;
+      d.ncarry = s->carry;
+      d.nnew = (int32_t)n;
+      d.final_ = close ? 1 : 0;
+      d.H = s->H;
+      d.D = s->ctx->D;
+      d.L = s->ctx->L;
+    }
+    PBVD_CUDA(e.launch(p, 32, st));
+  }
+  // host bookkeeping mirrors the kernel: whole periods decoded, segments
+  // released once their trigger stage exists, everything at close
+  for (size_t i = 0; i < count; ++i) {
+    pbvd_stream* s = ss[i];
+    const int64_t nst = s->carry + (int64_t)(n_stages ? n_stages[i] : 0);
+    const int64_t nproc = close ? nst : (nst / s->P) * s->P;
+    const int64_t tend = s->t + nproc;
+    const int64_t D = s->ctx->D, L = s->ctx->L;
+    int64_t nseg = 0;
+    if (tend >= s->released + D + L) nseg = (tend - L - s->released) / D;
+    s->t = tend;
+    s->released = close ? tend : s->released + nseg * D;
+    s->carry = (int)(nst - nproc);
+    if (close) s->closed = 1;
+  }
+  return PBVD_OK;
+}
+
+int pbvd_stream_push(pbvd_stream* s, const int8_t* d_llr, size_t n_stages, void* stream) {
+  return pbvd_stream_push_many(&s, &d_llr, &n_stages, 1, 0, stream);
+}
+
+int pbvd_stream_close(pbvd_stream* s, void* stream) {
+  return pbvd_stream_push_many(&s, nullptr, nullptr, 1, 1, stream);
 }
 
 }  // extern "C"

@@ -761,7 +761,7 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
                                             uint32_t* __restrict__ scratch, uint32_t* __restrict__ svs) {
   using S = Shape<C, T>;
   constexpr int R = C::R;
-  constexpr int M = S::M, P = S::P, CH = S::CH, RW = S::RW;
+  constexpr int M = S::M, P = S::P, CH = S::CH;
   const int lane = threadIdx.x & 31;
   const int tau = lane & (T - 1);
   const unsigned gmask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(T - 1)));

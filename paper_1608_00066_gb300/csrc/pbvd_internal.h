@@ -74,6 +74,41 @@ struct KernelEntry {
   AttrFn set_max_smem;
 };
 
+// One stream's push, as the stream kernel sees it.  The stages of the push
+// are the ncarry stages held back from the previous push (carry buffer)
+// followed by the nnew stages of the caller's buffer.
+struct StreamDev {
+  uint32_t* pm;          // N metric words (natural layout, lane A)
+  uint32_t* ring;        // H survivor records of RW words
+  int8_t* carry;         // up to P - 1 stages not yet decoded, R bytes each
+  const int8_t* llr;     // the caller's new stages, R bytes each
+  uint8_t* out;          // decoded bits of the whole stream
+  int64_t t0;            // first stage of this push (multiple of P)
+  int64_t released;      // first stage whose bits are not yet released
+  int32_t ncarry, nnew;
+  int32_t final_;        // 1: the stream ends here; decode and release all
+  int32_t H;             // ring records
+  int32_t D, L;
+};
+
+// Descriptors of up to kStreamsPerLaunch streams, passed by value as the
+// kernel parameter (so a launch owns its descriptors and can be captured).
+constexpr int kStreamsPerLaunch = 128;
+struct StreamLaunch {
+  int32_t count;
+  uint32_t one;          // 1, opaque to the compiler
+  StreamDev d[kStreamsPerLaunch];
+};
+
+using StreamLaunchFn = cudaError_t (*)(const StreamLaunch& p, int cta, cudaStream_t s);
+
+struct StreamKernelEntry {
+  int K, R, T, P;
+  uint32_t gens[3];
+  int words_per_stage;
+  StreamLaunchFn launch;
+};
+
 using BatchLaunchFn = cudaError_t (*)(const BatchArgs& a, int grid, int cta, size_t smem, cudaStream_t s);
 using BatchOccFn = cudaError_t (*)(int* blocks_per_sm, int cta, size_t smem);
 
@@ -94,5 +129,6 @@ int register_k7(KernelEntry* out, int cap);
 int register_k9(KernelEntry* out, int cap);
 int register_small(KernelEntry* out, int cap);
 int register_batch(BatchKernelEntry* out, int cap);
+int register_stream(StreamKernelEntry* out, int cap);
 
 }  // namespace pbvd

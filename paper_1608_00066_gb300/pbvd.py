@@ -34,6 +34,8 @@ EXPORTS = (
     "pbvd_set_config", "pbvd_get_config", "pbvd_strerror", "pbvd_last_cuda_error",
     "pbvd_decode_noalloc", "pbvd_noalloc_max_survivor_bytes",
     "pbvd_batch_prepare", "pbvd_batch_run", "pbvd_batch_destroy", "pbvd_autotune",
+    "pbvd_stream_open", "pbvd_stream_push", "pbvd_stream_push_many", "pbvd_stream_close",
+    "pbvd_stream_released", "pbvd_stream_destroy", "pbvd_batch_update",
 )
 
 
@@ -101,6 +103,8 @@ def load(path: Optional[str] = None):
         lib.pbvd_noalloc_max_survivor_bytes.restype = SZ
         lib.pbvd_batch_prepare.argtypes = [ctypes.POINTER(V), V, SZ, V]
         lib.pbvd_batch_prepare.restype = I
+        lib.pbvd_batch_update.argtypes = [V, V, SZ, I, V]
+        lib.pbvd_batch_update.restype = I
         lib.pbvd_batch_run.argtypes = [V, V]
         lib.pbvd_batch_run.restype = I
         lib.pbvd_batch_destroy.argtypes = [V]
@@ -108,6 +112,18 @@ def load(path: Optional[str] = None):
         lib.pbvd_autotune.argtypes = [V, V, SZ, V, V, I, ctypes.POINTER(pbvd_config),
                                       ctypes.POINTER(ctypes.c_float)]
         lib.pbvd_autotune.restype = I
+        lib.pbvd_stream_open.argtypes = [ctypes.POINTER(V), V, SZ, V, SZ]
+        lib.pbvd_stream_open.restype = I
+        lib.pbvd_stream_push.argtypes = [V, V, SZ, V]
+        lib.pbvd_stream_push.restype = I
+        lib.pbvd_stream_push_many.argtypes = [V, V, V, SZ, I, V]
+        lib.pbvd_stream_push_many.restype = I
+        lib.pbvd_stream_close.argtypes = [V, V]
+        lib.pbvd_stream_close.restype = I
+        lib.pbvd_stream_released.argtypes = [V]
+        lib.pbvd_stream_released.restype = ctypes.c_int64
+        lib.pbvd_stream_destroy.argtypes = [V]
+        lib.pbvd_stream_destroy.restype = None
         _lib = lib
         return lib
 
@@ -177,6 +193,21 @@ def _items(items):
     return arr
 
 
+def pbvd_batch_update(batch: int, items, reserve_sms: int = 0, stream: int = 0) -> None:
+    """Replaces the items of a prepared batch.  ``items`` is a sequence of
+    (ctx, d_llr, n_stages, d_out) or a C-contiguous uint64 numpy array of
+    shape (n, 4) in that column order (the layout of pbvd_batch_item)."""
+    import numpy as np
+    if isinstance(items, np.ndarray):
+        if items.dtype != np.uint64 or items.ndim != 2 or items.shape[1] != 4 or not items.flags.c_contiguous:
+            raise ValueError("items must be a C-contiguous uint64 array of shape (n, 4)")
+        ptr, n = items.ctypes.data, items.shape[0]
+    else:
+        arr = _items(items)
+        ptr, n = ctypes.cast(arr, ctypes.c_void_p).value, len(items)
+    _check(load().pbvd_batch_update(batch, ptr, n, reserve_sms, stream or None), "pbvd_batch_update")
+
+
 def pbvd_batch_prepare(items: Sequence[tuple], stream: int = 0) -> int:
     """Builds the work list of items (ctx, d_llr, n_stages, d_out); returns a
     batch handle for pbvd_batch_run / pbvd_batch_destroy."""
@@ -221,6 +252,37 @@ def pbvd_autotune(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int =
 
 def pbvd_strerror(code: int) -> str:
     return load().pbvd_strerror(code).decode()
+
+
+def pbvd_stream_open(ctx: int, max_push: int, d_out: int, out_capacity: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().pbvd_stream_open(ctypes.byref(h), ctx, max_push, d_out, out_capacity), "pbvd_stream_open")
+    return h.value
+
+
+def pbvd_stream_push(s: int, d_llr: int, n_stages: int, stream: int = 0) -> None:
+    _check(load().pbvd_stream_push(s, d_llr, n_stages, stream), "pbvd_stream_push")
+
+
+def pbvd_stream_push_many(handles: Sequence[int], d_llrs: Sequence[int], n_stages: Sequence[int],
+                          close: bool = False, stream: int = 0) -> None:
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*handles)
+    ps = (ctypes.c_void_p * n)(*[p or None for p in d_llrs])
+    ns = (ctypes.c_size_t * n)(*n_stages)
+    _check(load().pbvd_stream_push_many(hs, ps, ns, n, 1 if close else 0, stream), "pbvd_stream_push_many")
+
+
+def pbvd_stream_close(s: int, stream: int = 0) -> None:
+    _check(load().pbvd_stream_close(s, stream), "pbvd_stream_close")
+
+
+def pbvd_stream_released(s: int) -> int:
+    return int(load().pbvd_stream_released(s))
+
+
+def pbvd_stream_destroy(s: int) -> None:
+    load().pbvd_stream_destroy(s)
 
 
 # ------------------------------------------------------------- convenience
@@ -277,3 +339,46 @@ class Decoder:
         s = stream if stream is not None else torch.cuda.current_stream(llr.device)
         pbvd_decode(self.ctx, llr.data_ptr(), n_stages, out.data_ptr(), s.cuda_stream)
         return out
+
+
+class Stream:
+    """A continuous stream decoded with carried path metrics (torch tensors).
+
+    ``out`` is a uint8 CUDA tensor of ceil(capacity / 8) bytes that receives
+    the decoded bits; ``released`` is the number of leading stages whose bits
+    are final once the pushes so far have completed on their CUDA stream."""
+
+    def __init__(self, decoder: Decoder, capacity: int, max_push: int, device=None):
+        import torch
+        self.decoder = decoder
+        self.capacity = capacity
+        self.out = torch.zeros((capacity + 7) // 8, dtype=torch.uint8, device=device or "cuda")
+        self.handle = pbvd_stream_open(decoder.ctx, max_push, self.out.data_ptr(), capacity)
+
+    @property
+    def released(self) -> int:
+        return pbvd_stream_released(self.handle)
+
+    def push(self, llr, n_stages: int, stream=None):
+        import torch
+        if n_stages and (llr.dtype != torch.int8 or not llr.is_cuda or llr.dim() != 1 or not llr.is_contiguous()
+                         or llr.numel() < n_stages * len(self.decoder.gens)):
+            raise ValueError("llr must be a 1-D contiguous int8 CUDA tensor of R * n_stages values")
+        s = stream if stream is not None else torch.cuda.current_stream(self.out.device)
+        pbvd_stream_push(self.handle, llr.data_ptr() if n_stages else 0, n_stages, s.cuda_stream)
+
+    def close(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.out.device)
+        pbvd_stream_close(self.handle, s.cuda_stream)
+
+    def destroy(self):
+        if self.handle:
+            pbvd_stream_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
