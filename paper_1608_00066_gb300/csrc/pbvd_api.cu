@@ -935,7 +935,7 @@ int pbvd_stream_push_many(pbvd_stream* const* ss, const int8_t* const* d_llr, co
       d.D = s->ctx->D;
       d.L = s->ctx->L;
     }
-    PBVD_CUDA(e.launch(p, 32, st));
+    PBVD_CUDA(e.launch(p, st));
   }
   // host bookkeeping mirrors the kernel: whole periods decoded, segments
   // released once their trigger stage exists, everything at close

@@ -100,7 +100,7 @@ struct StreamLaunch {
   StreamDev d[kStreamsPerLaunch];
 };
 
-using StreamLaunchFn = cudaError_t (*)(const StreamLaunch& p, int cta, cudaStream_t s);
+using StreamLaunchFn = cudaError_t (*)(const StreamLaunch& p, cudaStream_t s);
 
 struct StreamKernelEntry {
   int K, R, T, P;
