@@ -147,6 +147,10 @@ __host__ __device__ constexpr int tb_kr() {
 }
 template <class C, int T>
 __host__ __device__ constexpr int tb_nbuf() { return T <= 2 ? 4 : 3; }
+// traceback: every lane walks both PBs of its pair (two chains) over 1/T of
+// the records, rather than half the lanes per PB
+template <class C, int T>
+__host__ __device__ constexpr bool tb_both_pbs() { return T >= 4; }
 template <class C, int T>
 __host__ __device__ constexpr int scratch_words_per_group() {
   using S = Shape<C, T>;
@@ -584,6 +588,32 @@ __device__ __forceinline__ int tb_step(int& psi, int& lm, int x, const uint32_t*
   return h;
 }
 
+// tb_step on a four-word record held in registers (RW == 4): the record can
+// be loaded before the state that indexes it is known, so the shared-memory
+// load leaves the step's dependency chain.
+template <class C, int T>
+__device__ __forceinline__ int tb_step4(int& psi, int& lm, int x, const uint4& rec) {
+  using S = Shape<C, T>;
+  static_assert(S::RW == 4, "four-word records");
+  constexpr int P = S::P;
+  constexpr int LMTOP = (1 << (P - 1)) - 1;
+  const int k = psi & (S::M - 1);
+  const int phb = lm + 1;
+  const int h = (k & phb) ? 1 : 0;
+  const int b = ((k >> 1) & ~lm) | (k & lm);
+  const int wi = (psi >> S::r) * S::W + (b >> S::LBPW);
+  const int bitpos = (((h << 1) | x) << 3) + 7 - (b & (S::BPW - 1));
+  const uint32_t lo = (wi & 1) ? rec.y : rec.x;
+  const uint32_t hi = (wi & 1) ? rec.w : rec.z;
+  const uint32_t word = (wi & 2) ? hi : lo;
+  const int upper = (word >> bitpos) & 1;
+  const int np = (psi & ~phb) | (upper ? 0 : phb);
+  const bool wrap = (lm == 0);
+  psi = wrap ? (int)rotl_v<C::v>((uint32_t)np, P % C::v) : np;
+  lm = wrap ? LMTOP : (lm >> 1);
+  return h;
+}
+
 // Global address of survivor record j of the group.
 template <class C, int T>
 __device__ __forceinline__ const uint32_t* global_record(const KArgs& a, int64_t gslot, int j) {
@@ -607,29 +637,64 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
   uint32_t acc[NCH];
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
-    lm[c] = (1 << ((L + min(hs, jend[c])) % P)) - 1;
+    lm[c] = (1 << ((L + max(0, min(hs, jend[c]))) % P)) - 1;
     acc[c] = 0u;
     g[c] = 0;
   }
   if (hs < lo) return;
+  auto emit = [&](int c, int j, int bit) {
+    acc[c] = (acc[c] << 1) | (uint32_t)bit;
+    if ((j & 7) == 0 && j <= emit_top[c]) {
+      const int rem = nout[c] - j;
+      const uint32_t keep = rem >= 8 ? 0xffu : ((1u << (rem > 0 ? rem : 0)) - 1u);
+      // the last 8 steps shifted in stages j + 7 .. j: bit q is stage j + q
+      dst[c][j >> 3] = (uint8_t)(acc[c] & keep);
+    }
+  };
   auto visit = [&](int j, const uint32_t* rec) {
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
       if (j <= jend[c]) {
         g[c] = (j == g_at) ? psi[c] : g[c];
-        const int bit = tb_step<C, T>(psi[c], lm[c], x[c], rec);
-        acc[c] = (acc[c] << 1) | (uint32_t)bit;
-        if ((j & 7) == 0 && j <= emit_top[c]) {
-          const int rem = nout[c] - j;
-          const uint32_t keep = rem >= 8 ? 0xffu : ((1u << (rem > 0 ? rem : 0)) - 1u);
-          // the last 8 steps shifted in stages j + 7 .. j: bit q is stage j + q
-          dst[c][j >> 3] = (uint8_t)(acc[c] & keep);
+        emit(c, j, tb_step<C, T>(psi[c], lm[c], x[c], rec));
+      }
+    }
+  };
+  // four-word records: r[q] = record jtop - q, all loaded before the walk
+  // through them (records below jbot are loaded but not visited)
+  auto visit4 = [&](int jtop, int jbot, const uint32_t* rec_top, int step) {
+    if constexpr (RW == 4) {
+      uint4 r[KR];
+#pragma unroll
+      for (int q = 0; q < KR; ++q) r[q] = *reinterpret_cast<const uint4*>(rec_top + q * step);
+#pragma unroll
+      for (int q = 0; q < KR; ++q) {
+        const int j = jtop - q;
+        if (j >= jbot) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) {
+            if (j <= jend[c]) {
+              g[c] = (j == g_at) ? psi[c] : g[c];
+              emit(c, j, tb_step4<C, T>(psi[c], lm[c], x[c], r[q]));
+            }
+          }
         }
       }
     }
   };
   if (a.smem_surv) {
-    for (int j = hs; j >= lo; --j) visit(j, svs + j * RW);
+    if constexpr (RW == 4) {
+      for (int jtop = hs; jtop >= lo; jtop -= KR) {
+        const int jbot = max(lo, jtop - KR + 1);
+        if (jtop - KR + 1 >= 0) {
+          visit4(jtop, jbot, svs + jtop * RW, -RW);
+        } else {
+          for (int j = jtop; j >= jbot; --j) visit(j, svs + j * RW);
+        }
+      }
+    } else {
+      for (int j = hs; j >= lo; --j) visit(j, svs + j * RW);
+    }
     return;
   }
   // ring: chunk ch holds records hs - ch*KR - q, q < KR, in buffer ch % NBUF
@@ -669,7 +734,11 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
     const int jtop = hs - ch * KR;
     const int jbot = max(lo, jtop - KR + 1);
     const uint32_t* buf = ring + (ch % NBUF) * (KR * RW);
-    for (int j = jtop; j >= jbot; --j) visit(j, buf + (jtop - j) * RW);
+    if constexpr (RW == 4) {
+      visit4(jtop, jbot, buf, RW);
+    } else {
+      for (int j = jtop; j >= jbot; --j) visit(j, buf + (jtop - j) * RW);
+    }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
@@ -695,60 +764,74 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     int psi[2] = {0, 0}, g[2];
     tb_walk<C, T, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
   } else {
-    // lanes [0, SPB) walk PB A, [SPB, 2 SPB) walk PB B (all lanes walk A if
-    // there is no B); segment s covers records [s*len, (s+1)*len - 1]
-    const int SPB = hasB ? T / 2 : T;
-    const int xb = (hasB && tau >= SPB) ? 1 : 0;
+    // Segments: lane tau walks segment s of the records of one or both PBs.
+    // With BOTH, every lane walks both PBs of the pair (two chains over the
+    // same records, two independent dependency chains per lane) over T
+    // segments; otherwise lanes [0, T/2) walk PB A and [T/2, T) PB B, one
+    // chain each (all lanes walk A when there is no B).
+    constexpr bool BOTH = tb_both_pbs<C, T>();
+    const int jA = gA.iend - L, jB = hasB ? gB.iend - L : -1;
+    const int SPB = BOTH ? T : (hasB ? T / 2 : T);
+    const int xb = (!BOTH && hasB && tau >= SPB) ? 1 : 0;
     const int s = tau - xb * SPB;
-    const PbRun& g0 = xb ? gB : gA;
-    const int jend = g0.iend - L;  // last record of this PB
-    const int seg = (((jend + 1 + SPB - 1) / SPB) + 7) & ~7;
+    const int jtop = BOTH ? max(jA, jB) : (xb ? jB : jA);
+    const int seg = (((jtop + 1 + SPB - 1) / SPB) + 7) & ~7;
     const int lo = s * seg;
-    const int hi = min(jend, lo + seg - 1);
-    const int stop = jend / seg;    // top non-empty segment
-    const bool active = lo <= jend;
-    const int hs = (s == stop) ? jend : min(jend, hi + TS::LAMBDA);
-    int psi[1] = {0}, g[1] = {0};
-    {
-      const int emit_top[1] = {min(hi, g0.nout - 1)};
-      const int je[1] = {jend};
-      const int x[1] = {xb};
-      const int nout[1] = {g0.nout};
-      uint8_t* const dst[1] = {g0.dst};
-      if (active) tb_walk<C, T, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
+    const int hi = min(jtop, lo + seg - 1);
+    const int stop = jtop / seg;    // top non-empty segment
+    const bool active = lo <= jtop;
+    const int hs = (s == stop) ? jtop : min(jtop, hi + TS::LAMBDA);
+    int psi[2] = {0, 0}, g[2] = {0, 0};
+    if (active) {
+      if constexpr (BOTH) {
+        const int emit_top[2] = {min(hi, gA.nout - 1), min(hi, gB.nout - 1)};
+        const int je[2] = {jA, jB};
+        const int x[2] = {0, 1};
+        const int nout[2] = {gA.nout, gB.nout};
+        uint8_t* const dst[2] = {gA.dst, gB.dst};
+        tb_walk<C, T, 2>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
+      } else {
+        const PbRun& g0 = xb ? gB : gA;
+        const int emit_top[1] = {min(hi, g0.nout - 1)};
+        const int je[1] = {jtop};
+        const int x[1] = {xb};
+        const int nout[1] = {g0.nout};
+        uint8_t* const dst[1] = {g0.dst};
+        int p1[1] = {0}, g1[1] = {0};
+        tb_walk<C, T, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
+        psi[0] = p1[0];
+        g[0] = g1[0];
+      }
     }
-    // top-down check of the guessed segments of each PB in turn
+    // top-down check of the guessed segments of each PB: segment q is exact
+    // if the state its walk held at record hi_q equals the exact exit state
+    // of segment q + 1; otherwise it is walked again from that state (rare).
+    // A chain whose last record lies in segment q started there exactly.
     for (int pb = 0; pb < (hasB ? 2 : 1); ++pb) {
       const PbRun& gp = pb ? gB : gA;
-      const int jend_p = gp.iend - L;
-      const int seg_p = (((jend_p + 1 + SPB - 1) / SPB) + 7) & ~7;
+      const int jend_p = pb ? jB : jA;
+      const int seg_p = BOTH ? seg : (((jend_p + 1 + SPB - 1) / SPB) + 7) & ~7;
       const int top = jend_p / seg_p;
-      const int base = pb * SPB;
-      int exact = __shfl_sync(gmask, psi[0], base + top, T);
+      const int base = BOTH ? 0 : pb * SPB;   // lane of segment 0
+      const int c = BOTH ? pb : 0;            // chain of this PB in its lanes
+      int exact = __shfl_sync(gmask, c ? psi[1] : psi[0], base + top, T);
       for (int q = top - 1; q >= 0; --q) {
-        const int gq = __shfl_sync(gmask, g[0], base + q, T);
-        int ex = __shfl_sync(gmask, psi[0], base + q, T);
+        const int gq = __shfl_sync(gmask, c ? g[1] : g[0], base + q, T);
+        int ex = __shfl_sync(gmask, c ? psi[1] : psi[0], base + q, T);
         if (gq != exact) {
-          // re-walk segment q from the exact state (rare)
           if (tau == base + q) {
+            // the same prefetched walk as above, from the exact state
             const int lo_q = q * seg_p, hi_q = min(jend_p, lo_q + seg_p - 1);
-            int p2 = exact;
-            int lm2 = (1 << ((L + hi_q) % Shape<C, T>::P)) - 1;
-            uint32_t acc2 = 0u;
-            for (int j = hi_q; j >= lo_q; --j) {
-              const uint32_t* rec = a.smem_surv ? svs + j * Shape<C, T>::RW : global_record<C, T>(a, gslot, j);
-              const int bit = tb_step<C, T>(p2, lm2, pb, rec);
-              if (j < gp.nout) {
-                acc2 |= (uint32_t)bit << (j & 7);
-                if ((j & 7) == 0) {
-                  gp.dst[j >> 3] = (uint8_t)acc2;
-                  acc2 = 0u;
-                }
-              }
-            }
-            psi[0] = p2;
+            int p2[1] = {exact}, g2[1];
+            const int emit_top[1] = {min(hi_q, gp.nout - 1)};
+            const int je[1] = {jend_p};
+            const int x[1] = {pb};
+            const int nout[1] = {gp.nout};
+            uint8_t* const dst[1] = {gp.dst};
+            tb_walk<C, T, 1>(a, gslot, svs, ring, L, hi_q, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
+            if (c) psi[1] = p2[0]; else psi[0] = p2[0];
           }
-          ex = __shfl_sync(gmask, psi[0], base + q, T);
+          ex = __shfl_sync(gmask, c ? psi[1] : psi[0], base + q, T);
         }
         exact = ex;
       }
