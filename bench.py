@@ -291,6 +291,7 @@ def run_ours(args, rank: int, world: int):
 
     batched = run_batched(args) if (rank == 0 and not args.no_batch) else None
     latency = run_latency(args) if (rank == 0 and not args.no_batch) else None
+    k9 = run_k9(args) if (rank == 0 and not args.no_batch) else None
 
     value = aggregate_gbps(K_INFO, world, ms)
     e2e = aggregate_gbps(K_INFO, world, e2e_ms)
@@ -316,6 +317,7 @@ def run_ours(args, rank: int, world: int):
         "ber": ber,
         "batched_vs_plain": batched,
         "latency": latency,
+        "k9_stream": k9,
         "paper_context": PAPER_CONTEXT,
     }
     return result, frame
@@ -405,6 +407,130 @@ def run_latency(args):
             "p50_us": round(1000 * ts[len(ts) // 2], 1), "p99_us": round(1000 * ts[int(len(ts) * 0.99) - 1], 1)}
 
 
+def time_decode(dec, d_llr, n, d_out, steps: int, warmup: int, flush):
+    """Mean device time (ms) of one decode of the whole stream, L2 flushed
+    between steps (outside the events), after warm-up."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        dec.decode(d_llr, n, d_out, stream=stream)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dec.decode(d_llr, n, d_out, stream=stream)
+        e1.record(stream)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ts) / len(ts)
+
+
+def run_k9(args):
+    """The 256-state code: K=9 rate-1/3 (557,663,711) terminated stream of
+    2^24 information bits at Eb/N0 = 2 dB, D=1024, L=64; device-resident
+    decode with the tuned kernel configuration."""
+    import torch
+    from paper_1608_00066_gb300 import pbvd, synth
+    spec = synth.K9_R13
+    D, L = 1024, 64
+    f = synth.make_frame(spec, K_INFO, 2.0, seed=3001)
+    n = f.n_stages
+    dec = pbvd.Decoder(spec.K, spec.gens, None, D, L)
+    d_llr = torch.from_numpy(f.llr).cuda()
+    d_out = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
+    dec.autotune(d_llr, n, d_out, reps=3)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ms = time_decode(dec, d_llr, n, d_out, max(5, args.steps), max(3, args.warmup), flush)
+    bits = np.unpackbits(d_out.cpu().numpy(), bitorder="little")[:K_INFO]
+    ops_bit = algorithmic_ops_per_bit(256, D, L)
+    achieved = ops_bit * K_INFO / (ms * 1e-3)
+    cfg = dec.get_config(n)
+    dec.close()
+    return {"workload": "K9 r1/3 (557,663,711) terminated stream, 2^24 info bits, Eb/N0 2 dB, D=1024 L=64",
+            "gbps": round(K_INFO / ms / 1e6, 3), "ms": round(ms, 4), "kernel_config": cfg,
+            "ops_per_bit": ops_bit, "roofline_frac": round(achieved / peak_int16_ops(), 4),
+            "ber": float((bits != f.msg).mean())}
+
+
+SWEEP_EBN0 = (0, 1, 2, 3, 4, 5, 6)
+SWEEP_D = (256, 512, 1024, 2048)
+SWEEP_L = (35, 42, 64)
+
+
+def _sweep_frame(ebn0: int):
+    from paper_1608_00066_gb300 import synth
+    return synth.make_frame(synth.K7_R12, K_INFO, float(ebn0), seed=2000 + ebn0)
+
+
+def _full_frame_ber(ebn0: int):
+    """Child process: bit error rate of the full-frame CPU Viterbi decoder
+    (maximum likelihood, no blocking) on the sweep stream at one Eb/N0."""
+    sys.path.insert(0, ROOT)
+    import oracle as orc
+    f = _sweep_frame(ebn0)
+    t0 = time.perf_counter()
+    bits, _ = orc.viterbi_full(7, (0o171, 0o133), f.llr.reshape(-1, 2))
+    return ebn0, int((bits[:K_INFO] != f.msg).sum()), time.perf_counter() - t0
+
+
+def run_sweep(args):
+    """The K=7 r1/2 stream of 2^24 information bits at Eb/N0 = 0..6 dB, each
+    decoded with D in {256, 512, 1024, 2048} and L in {35, 42, 64}: device
+    throughput (tuned kernel configuration, L2 flushed between steps), bit
+    errors of the block decoder, bit errors of the full-frame decoder (CPU,
+    in spawned processes) so that the truncation loss of the blocks is shown,
+    and a sampled bit-exact check of every run against the block oracle
+    (first, last and two random blocks)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(min(len(SWEEP_EBN0), os.cpu_count() or 1))
+    full = pool.map_async(_full_frame_ber, SWEEP_EBN0)
+    import torch
+    import oracle as orc
+    from paper_1608_00066_gb300 import build as pbuild
+    from paper_1608_00066_gb300 import pbvd
+    pbuild.build()
+    orc.build()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    gens = (0o171, 0o133)
+    rows = []
+    for e in SWEEP_EBN0:
+        f = _sweep_frame(e)
+        n = f.n_stages
+        llr2 = f.llr.reshape(n, 2)
+        d_llr = torch.from_numpy(f.llr).cuda()
+        d_out = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        for D in SWEEP_D:
+            for L in SWEEP_L:
+                dec = pbvd.Decoder(7, gens, None, D, L)
+                dec.autotune(d_llr, n, d_out, reps=2)
+                ms = time_decode(dec, d_llr, n, d_out, max(3, args.steps), 2, flush)
+                got = np.unpackbits(d_out.cpu().numpy(), bitorder="little")[:n]
+                nb = (n + D - 1) // D
+                rng = np.random.default_rng(1000 * e + D + L)
+                picks = sorted({0, nb - 1, *(int(x) for x in rng.integers(1, nb - 1, size=2))})
+                exact = True
+                for b in picks:
+                    want = orc.viterbi_block(7, gens, llr2, D, L, blocks=(b, b + 1))
+                    o0, o1 = b * D, min((b + 1) * D, n)
+                    exact &= bool(np.array_equal(got[o0:o1], want[o0:o1]))
+                rows.append({"ebn0_db": e, "D": D, "L": L, "gbps": round(K_INFO / ms / 1e6, 3),
+                             "ms": round(ms, 4), "bit_errors": int((got[:K_INFO] != f.msg).sum()),
+                             "kernel_config": dec.get_config(n), "sampled_blocks_exact": exact})
+                dec.close()
+        del d_llr, d_out
+    full_res = {e: (errs, secs) for e, errs, secs in full.get()}
+    pool.close()
+    for r in rows:
+        r["full_frame_bit_errors"] = full_res[r["ebn0_db"]][0]
+        r["ber"] = r["bit_errors"] / K_INFO
+        r["full_frame_ber"] = r["full_frame_bit_errors"] / K_INFO
+    return {"sweep": "K7 r1/2 (171,133) stream, 2^24 info bits, seed 2000 + Eb/N0; D x L x Eb/N0",
+            "info_bits": K_INFO, "rows": rows,
+            "full_frame_cpu_seconds": {str(e): round(full_res[e][1], 2) for e in SWEEP_EBN0}}
+
+
 SERVE_RATES = (0.5e6, 1.0e6, 2.0e6, 4.0e6)   # offered frames/s
 SERVE_WINDOW_S = 0.25
 
@@ -458,12 +584,18 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and latency extras")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the benchmark line: BER and throughput over Eb/N0 x D x L (one JSON line)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps(run_sweep(args)), flush=True)
         return
 
     if world > 1:
