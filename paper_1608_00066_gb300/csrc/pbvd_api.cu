@@ -34,7 +34,7 @@ int cuda_fail(cudaError_t e) {
 
 struct Registry {
   std::vector<KernelEntry> entries;
-  std::vector<int> smem_set;  // max dynamic smem already granted per entry
+  std::vector<int> smem_set;  // max dynamic smem already granted per entry and survivor placement
   std::vector<BatchKernelEntry> batch;
   std::vector<int> batch_smem_set;
   std::vector<StreamKernelEntry> stream;
@@ -47,10 +47,11 @@ Registry& registry() {
     KernelEntry buf[64];
     int n = 0;
     n += register_k7(buf + n, 64 - n);
+    n += register_k7_punctured(buf + n, 64 - n);
     n += register_k9(buf + n, 64 - n);
     n += register_small(buf + n, 64 - n);
     reg.entries.assign(buf, buf + n);
-    reg.smem_set.assign(n, 48 * 1024);
+    reg.smem_set.assign(2 * n, 48 * 1024);
     BatchKernelEntry bb[4];
     const int nb = register_batch(bb, 4);
     reg.batch.assign(bb, bb + nb);
@@ -181,12 +182,13 @@ int ensure_work(pbvd_ctx* c, size_t bytes) {
   return PBVD_OK;
 }
 
-int grant_smem(int entry, size_t bytes) {
+int grant_smem(int entry, bool smem_surv, size_t bytes) {
   Registry& reg = registry();
   std::lock_guard<std::mutex> lk(g_reg_mu);
-  if ((int)bytes <= reg.smem_set[entry]) return PBVD_OK;
-  PBVD_CUDA(reg.entries[entry].set_max_smem((int)bytes));
-  reg.smem_set[entry] = (int)bytes;
+  const int slot = 2 * entry + (smem_surv ? 1 : 0);
+  if ((int)bytes <= reg.smem_set[slot]) return PBVD_OK;
+  PBVD_CUDA(reg.entries[entry].set_max_smem[smem_surv ? 1 : 0]((int)bytes));
+  reg.smem_set[slot] = (int)bytes;
   return PBVD_OK;
 }
 
@@ -557,7 +559,7 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
     rc = ensure_work(c, p.surv_bytes);
     if (rc != PBVD_OK) return rc;
   }
-  rc = grant_smem(p.entry, p.smem_bytes);
+  rc = grant_smem(p.entry, p.smem_surv != 0, p.smem_bytes);
   if (rc != PBVD_OK) return rc;
   KArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -584,7 +586,7 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   const int64_t grid = ceil_div(p.n_pairs, p.groups);
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
-  PBVD_CUDA(e.launch(a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
+  PBVD_CUDA(e.launch[p.smem_surv ? 1 : 0](a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
   return PBVD_OK;
 }
 
@@ -714,7 +716,7 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   uint32_t* surv = nullptr;
   rc = noalloc_survivors(dev, &surv);
   if (rc != PBVD_OK) return rc;
-  rc = grant_smem(p.entry, p.smem_bytes);
+  rc = grant_smem(p.entry, p.smem_surv != 0, p.smem_bytes);
   if (rc != PBVD_OK) return rc;
   KArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -741,7 +743,7 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   const int64_t grid = ceil_div(p.n_pairs, p.groups);
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
-  PBVD_CUDA(e.launch(a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
+  PBVD_CUDA(e.launch[p.smem_surv ? 1 : 0](a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
   return PBVD_OK;
 }
 

@@ -450,13 +450,16 @@ struct PairWork {
 
 // One period (P stages starting at lock-step index i0) of the forward pass.
 // CHECKED = false: every stage of the period is inside both PBs' forward
-// ranges (or B does not exist) and no re-initialisation falls inside.
-template <class C, int T, bool CHECKED, bool PUNCT>
+// ranges (or B does not exist) and no re-initialisation falls inside; then
+// STORE says whether all of its stages (i >= L) or none of them keep
+// survivor records, so the period is one branch-free basic block.  SMEM:
+// records go to shared memory (ssv), else to the global workspace (gsv).
+template <class C, int T, bool CHECKED, bool PUNCT, bool SMEM, bool STORE>
 __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], const uint32_t (&sel)[Shape<C, T>::P][3],
                                                const KArgs& a, const int8_t* bufA, int cbA, const int8_t* bufB,
                                                int cbB, bool hasB, int i0, int I, int L, int tau, PbRun& gA,
                                                PbRun& gB, uint32_t*& gsv, int64_t rec_stride, uint32_t*& ssv,
-                                               bool smem_surv, const PipeConsts& pc) {
+                                               const PipeConsts& pc) {
   using S = Shape<C, T>;
   constexpr int W = S::W;
   constexpr int R = C::R;
@@ -512,8 +515,8 @@ __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], c
     if constexpr (S::P > 5) if (ph == 5) acs_stage<C, T, (S::P > 5 ? 5 : 0)>(pm, wd, bm, kt, pc);
     if constexpr (S::P > 6) if (ph == 6) acs_stage<C, T, (S::P > 6 ? 6 : 0)>(pm, wd, bm, kt, pc);
     if constexpr (S::P > 7) if (ph == 7) acs_stage<C, T, (S::P > 7 ? 7 : 0)>(pm, wd, bm, kt, pc);
-    if (i >= L) {
-      if (smem_surv) {
+    if (CHECKED ? (i >= L) : STORE) {
+      if constexpr (SMEM) {
 #pragma unroll
         for (int w = 0; w < W; ++w) ssv[w] = wd[w];
         ssv += S::RW;
@@ -626,7 +629,7 @@ __device__ __forceinline__ const uint32_t* global_record(const KArgs& a, int64_t
 // survivor region svs in shared-memory mode, else a per-lane ring that is
 // filled with cp.async KR records at a time.  On return psi is the exit
 // state and g the state held on arrival at record g_at.
-template <class C, int T, int NCH>
+template <class C, int T, bool SMEM, int NCH>
 __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uint32_t* svs, uint32_t* ring,
                                         int L, int hs, int lo, const int (&emit_top)[NCH], const int (&jend)[NCH],
                                         const int (&x)[NCH], const int (&nout)[NCH], uint8_t* const (&dst)[NCH],
@@ -682,7 +685,7 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
       }
     }
   };
-  if (a.smem_surv) {
+  if constexpr (SMEM) {
     if constexpr (RW == 4) {
       for (int jtop = hs; jtop >= lo; jtop -= KR) {
         const int jbot = max(lo, jtop - KR + 1);
@@ -743,7 +746,7 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <class C, int T>
+template <class C, int T, bool SMEM>
 __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, const PbRun& gB, bool hasB, int J,
                                                int64_t gslot, uint32_t* scratch, const uint32_t* svs) {
   using TS = TbShape<C, T>;
@@ -762,7 +765,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     const int nout[2] = {gA.nout, gB.nout};
     uint8_t* const dst[2] = {gA.dst, gB.dst};
     int psi[2] = {0, 0}, g[2];
-    tb_walk<C, T, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
+    tb_walk<C, T, SMEM, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
   } else {
     // Segments: lane tau walks segment s of the records of one or both PBs.
     // With BOTH, every lane walks both PBs of the pair (two chains over the
@@ -789,7 +792,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
         const int x[2] = {0, 1};
         const int nout[2] = {gA.nout, gB.nout};
         uint8_t* const dst[2] = {gA.dst, gB.dst};
-        tb_walk<C, T, 2>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
+        tb_walk<C, T, SMEM, 2>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
       } else {
         const PbRun& g0 = xb ? gB : gA;
         const int emit_top[1] = {min(hi, g0.nout - 1)};
@@ -798,7 +801,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
         const int nout[1] = {g0.nout};
         uint8_t* const dst[1] = {g0.dst};
         int p1[1] = {0}, g1[1] = {0};
-        tb_walk<C, T, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
+        tb_walk<C, T, SMEM, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
         psi[0] = p1[0];
         g[0] = g1[0];
       }
@@ -828,7 +831,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
             const int x[1] = {pb};
             const int nout[1] = {gp.nout};
             uint8_t* const dst[1] = {gp.dst};
-            tb_walk<C, T, 1>(a, gslot, svs, ring, L, hi_q, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
+            tb_walk<C, T, SMEM, 1>(a, gslot, svs, ring, L, hi_q, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
             if (c) psi[1] = p2[0]; else psi[0] = p2[0];
           }
           ex = __shfl_sync(gmask, c ? psi[1] : psi[0], base + q, T);
@@ -839,7 +842,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
   }
 }
 
-template <class C, int T, bool PUNCT>
+template <class C, int T, bool PUNCT, bool SMEM>
 __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, int64_t gslot,
                                             uint32_t* __restrict__ scratch, uint32_t* __restrict__ svs) {
   using S = Shape<C, T>;
@@ -912,12 +915,16 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
     const int8_t* bufA = raw + cur * 2 * CB;
     const int8_t* bufB = bufA + CB;
     const int cbA = cur ? cbA1 : cbA0, cbB = cur ? cbB1 : cbB0;
-    if (i0 >= fast_lo && i0 <= fast_hi)
-      forward_period<C, T, false, PUNCT>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA, gB, gsv,
-                                         rec_stride, ssv, a.smem_surv, pc);
+    const bool fast = i0 >= fast_lo && i0 <= fast_hi;
+    if (fast && i0 >= L)
+      forward_period<C, T, false, PUNCT, SMEM, true>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
+                                                     gB, gsv, rec_stride, ssv, pc);
+    else if (fast && i0 + P <= L)
+      forward_period<C, T, false, PUNCT, SMEM, false>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
+                                                      gB, gsv, rec_stride, ssv, pc);
     else
-      forward_period<C, T, true, PUNCT>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA, gB, gsv,
-                                        rec_stride, ssv, a.smem_surv, pc);
+      forward_period<C, T, true, PUNCT, SMEM, true>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
+                                                    gB, gsv, rec_stride, ssv, pc);
     if (i0 + P < I) {
       // end of a full period: transpose back to psi = u (T > 1)
       if constexpr (vector_transpose<C, T>()) {
@@ -970,11 +977,12 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 
-  traceback_pair<C, T>(a, gA, gB, wk.hasB, J, gslot, scratch, svs);
+  traceback_pair<C, T, SMEM>(a, gA, gB, wk.hasB, J, gslot, scratch, svs);
 }
 
-// Plain launch: pair p of one stream.
-template <class C, int T, bool PUNCT>
+// Plain launch: pair p of one stream.  SMEM: survivor records of each group
+// in shared memory (a.smem_rec_words words per group), else in a.surv.
+template <class C, int T, bool PUNCT, bool SMEM>
 __global__ void __launch_bounds__(256, 1) pbvd_decode_kernel(const KArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int groups_per_cta = blockDim.x / T;
@@ -993,7 +1001,7 @@ __global__ void __launch_bounds__(256, 1) pbvd_decode_kernel(const KArgs a) {
   wk.B = wk.A;
   wk.B.b = 2 * pair + 1;
   wk.hasB = (2 * pair + 1) < a.n_blocks;
-  decode_pair<C, T, PUNCT>(a, wk, pair, scratch, svs);
+  decode_pair<C, T, PUNCT, SMEM>(a, wk, pair, scratch, svs);
 }
 
 }  // namespace pbvd

@@ -5,15 +5,16 @@
 
 namespace pbvd {
 
-template <class C, int T, bool PUNCT>
+template <class C, int T, bool PUNCT, bool SMEM>
 cudaError_t launch_decode(const KArgs& a, int grid, int cta, size_t smem, cudaStream_t s) {
-  pbvd_decode_kernel<C, T, PUNCT><<<grid, cta, smem, s>>>(a);
+  pbvd_decode_kernel<C, T, PUNCT, SMEM><<<grid, cta, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <class C, int T, bool PUNCT>
+template <class C, int T, bool PUNCT, bool SMEM>
 cudaError_t set_max_smem(int bytes) {
-  return cudaFuncSetAttribute(pbvd_decode_kernel<C, T, PUNCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(pbvd_decode_kernel<C, T, PUNCT, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
 }
 
 template <class C, int T, bool PUNCT = false>
@@ -28,8 +29,10 @@ KernelEntry make_entry() {
   e.punct = PUNCT;
   e.words_per_stage = record_words_per_stage<C, T>();
   e.scratch_words = scratch_words_per_group<C, T>();
-  e.launch = &launch_decode<C, T, PUNCT>;
-  e.set_max_smem = &set_max_smem<C, T, PUNCT>;
+  e.launch[0] = &launch_decode<C, T, PUNCT, false>;
+  e.launch[1] = &launch_decode<C, T, PUNCT, true>;
+  e.set_max_smem[0] = &set_max_smem<C, T, PUNCT, false>;
+  e.set_max_smem[1] = &set_max_smem<C, T, PUNCT, true>;
   return e;
 }
 

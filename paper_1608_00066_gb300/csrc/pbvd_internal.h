@@ -70,8 +70,8 @@ struct KernelEntry {
   bool punct;              // built for punctured input
   int words_per_stage;     // survivor record words per stage per pair (T * W)
   int scratch_words;       // shared-memory words per group besides records
-  LaunchFn launch;
-  AttrFn set_max_smem;
+  LaunchFn launch[2];      // [0]: records in the global workspace, [1]: in shared memory
+  AttrFn set_max_smem[2];
 };
 
 // One stream's push, as the stream kernel sees it.  The stages of the push
@@ -126,6 +126,7 @@ struct BatchKernelEntry {
 
 // Registries filled by the instance files.
 int register_k7(KernelEntry* out, int cap);
+int register_k7_punctured(KernelEntry* out, int cap);
 int register_k9(KernelEntry* out, int cap);
 int register_small(KernelEntry* out, int cap);
 int register_batch(BatchKernelEntry* out, int cap);
