@@ -41,6 +41,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "pbvd_internal.h"
@@ -139,14 +140,23 @@ __host__ __device__ constexpr int transpose_words() {
 }
 template <class C, int T>
 __host__ __device__ constexpr int raw_offset_words() { return transpose_words<C, T>(); }
-// traceback ring per lane: NBUF chunks of KR records of RW words
+// traceback ring per lane: NBUF chunks of KR records of RW words.  Four-word
+// records (the v = 6 codes with T <= 4) are walked a period at a time, so a
+// chunk is one period and the ring keeps about 24 records in flight.
 template <class C, int T>
-__host__ __device__ constexpr int tb_kr() {
-  return T <= 2 ? ((32 / Shape<C, T>::RW) > 1 ? (32 / Shape<C, T>::RW) : 1)
-                : ((16 / Shape<C, T>::RW) > 1 ? (16 / Shape<C, T>::RW) : 1);
+__host__ __device__ constexpr bool tb_period_walk() {
+  return Shape<C, T>::RW == 4 && C::v == 6;
 }
 template <class C, int T>
-__host__ __device__ constexpr int tb_nbuf() { return T <= 2 ? 4 : 3; }
+__host__ __device__ constexpr int tb_kr() {
+  return tb_period_walk<C, T>() ? Shape<C, T>::P
+         : T <= 2 ? ((32 / Shape<C, T>::RW) > 1 ? (32 / Shape<C, T>::RW) : 1)
+                  : ((16 / Shape<C, T>::RW) > 1 ? (16 / Shape<C, T>::RW) : 1);
+}
+template <class C, int T>
+__host__ __device__ constexpr int tb_nbuf() {
+  return tb_period_walk<C, T>() ? 1 + (24 + Shape<C, T>::P - 1) / Shape<C, T>::P : (T <= 2 ? 4 : 3);
+}
 // traceback: every lane walks both PBs of its pair (two chains) over 1/T of
 // the records, rather than half the lanes per PB
 template <class C, int T>
@@ -354,7 +364,7 @@ __device__ __forceinline__ uint32_t decision_bytes(uint32_t t0, uint32_t t1) {
 }
 
 // Merges the byte masks d[lo..lo+n) of consecutive butterflies into one
-// word: butterfly q's decisions end up at bit 7 - q of every byte.  The masks
+// word: butterfly q's decisions end up at bit q of every byte.  The masks
 // are all-zero or all-one bytes, so a select with a constant needs no shift.
 template <int LO, int N>
 __device__ __forceinline__ uint32_t merge_decisions(const uint32_t* d) {
@@ -363,7 +373,7 @@ __device__ __forceinline__ uint32_t merge_decisions(const uint32_t* d) {
   } else {
     const uint32_t a = merge_decisions<LO, N / 2>(d);
     const uint32_t b = merge_decisions<LO + N / 2, N / 2>(d);
-    constexpr uint32_t byte = ((1u << (N / 2)) - 1u) << (8 - LO - N);
+    constexpr uint32_t byte = ((1u << (N / 2)) - 1u) << (LO + N / 2);
     constexpr uint32_t m = byte * 0x01010101u;
     return (a & ~m) | (b & m);
   }
@@ -371,9 +381,9 @@ __device__ __forceinline__ uint32_t merge_decisions(const uint32_t* d) {
 
 // One trellis stage at phase PH for the thread's M registers, in place.
 // Butterfly b (the b-th register k0 with bit PH clear, k1 = k0 | 1 << PH)
-// stores its four decision bits in survivor word b / BPW at bits 7 - q
-// (PB A of k0), 15 - q (PB B of k0), 23 - q (PB A of k1), 31 - q (PB B of
-// k1), q = b % BPW; a set bit means the upper branch was kept.
+// stores its four decision bits in survivor word b / BPW at bits q (PB A of
+// k0), 8 + q (PB B of k0), 16 + q (PB A of k1), 24 + q (PB B of k1),
+// q = b % BPW; a set bit means the upper branch was kept.
 // Per butterfly: two fused add-min (ALU), two candidate adds (FMA), one
 // decision difference on each pipe, one byte permute and 7/8 of a select
 // (ALU) for the decision bits.
@@ -537,19 +547,6 @@ __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], c
   }
 }
 
-// Survivor bit of the state at physical index psi in a stage record at
-// phase mask lm = (1 << ph) - 1 (see acs_stage for the layout).
-template <class C, int T>
-__device__ __forceinline__ int record_bit(const uint32_t* __restrict__ rec, int psi, int lm, int x) {
-  using S = Shape<C, T>;
-  const int k = psi & (S::M - 1);
-  const int h = (k & (lm + 1)) ? 1 : 0;
-  const int b = ((k >> 1) & ~lm) | (k & lm);
-  const int word = (psi >> S::r) * S::W + (b >> S::LBPW);
-  const int bit = (((h << 1) | x) << 3) + 7 - (b & (S::BPW - 1));
-  return (rec[word] >> bit) & 1;
-}
-
 // ------------------------------------------------------------- traceback --
 
 // Traceback shape.  T == 1: the lane walks both PBs of its pair (two chains,
@@ -582,7 +579,7 @@ __device__ __forceinline__ int tb_step(int& psi, int& lm, int x, const uint32_t*
   const int h = (k & phb) ? 1 : 0;
   const int b = ((k >> 1) & ~lm) | (k & lm);
   const int wi = (psi >> S::r) * S::W + (b >> S::LBPW);
-  const int bitpos = (((h << 1) | x) << 3) + 7 - (b & (S::BPW - 1));
+  const int bitpos = (((h << 1) | x) << 3) + (b & (S::BPW - 1));
   const int upper = (rec[wi] >> bitpos) & 1;
   const int np = (psi & ~phb) | (upper ? 0 : phb);
   const bool wrap = (lm == 0);
@@ -605,7 +602,7 @@ __device__ __forceinline__ int tb_step4(int& psi, int& lm, int x, const uint4& r
   const int h = (k & phb) ? 1 : 0;
   const int b = ((k >> 1) & ~lm) | (k & lm);
   const int wi = (psi >> S::r) * S::W + (b >> S::LBPW);
-  const int bitpos = (((h << 1) | x) << 3) + 7 - (b & (S::BPW - 1));
+  const int bitpos = (((h << 1) | x) << 3) + (b & (S::BPW - 1));
   const uint32_t lo = (wi & 1) ? rec.y : rec.x;
   const uint32_t hi = (wi & 1) ? rec.w : rec.z;
   const uint32_t word = (wi & 2) ? hi : lo;
@@ -746,6 +743,173 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+
+// ----------------------------------------------- period-unrolled traceback --
+//
+// For four-word records (v = 6, T * NB = 32 butterflies per stage and PB
+// pair) the survivor bit of the state at physical index psi in a record of
+// phase ph sits at word B >> 3, byte 2h + x, bit B & 7, where B is psi with
+// bit ph deleted (5 bits) and h = bit ph of psi.  gather4 moves the 64 bits
+// of PB x into one 64-bit value G whose byte g holds record word g >> 1,
+// byte 2 (g & 1) + x, i.e. bit (B4 B3 h B2 B1 B0) of G; at phase 4 the bytes
+// are ordered (B4, h, B3) instead.  Then the bit of psi is bit conv4(psi)
+// of G, and conv4 is the identity at phases 3 and 4.
+template <int PH>
+__device__ __forceinline__ uint64_t gather4(const uint4& rec, int x) {
+  const uint32_t sel = PH == 4 ? (x ? 0x7351u : 0x6240u) : (x ? 0x7531u : 0x6420u);
+  const uint32_t g0 = __byte_perm(rec.x, rec.y, sel);
+  const uint32_t g1 = __byte_perm(rec.z, rec.w, sel);
+  return ((uint64_t)g1 << 32) | g0;
+}
+
+template <int PH>
+__device__ __forceinline__ uint32_t conv4(uint32_t psi) {
+  if constexpr (PH == 3 || PH == 4) {
+    return psi;
+  } else if constexpr (PH == 5) {
+    // B = (p4 p3 p2 p1 p0), h = p5: bit index (p4 p3 p5 p2 p1 p0)
+    return ((psi << 1) & 0x30u) | ((psi >> 2) & 0x8u) | (psi & 0x7u);
+  } else {
+    // B = (p5 p4 [p3 p2 p1 p0 without p_PH]), h = p_PH
+    const uint32_t low = psi & ((1u << PH) - 1u);
+    const uint32_t mid = (psi >> (PH + 1)) & ((1u << (3 - PH)) - 1u);
+    return (psi & 0x30u) | (((psi >> PH) & 1u) << 3) | (mid << PH) | low;
+  }
+}
+
+// One traceback step at a record of compile-time phase PH: appends the
+// decoded bit (bit PH of psi) to acc and moves psi to the predecessor (bit
+// PH replaced by the survivor's branch, then the period rotation at PH = 0).
+template <class C, int T, int PH>
+__device__ __forceinline__ void tb_step_ph(uint32_t& psi, uint32_t& acc, uint64_t G) {
+  constexpr int P = Shape<C, T>::P;
+  const uint32_t upper = (uint32_t)(G >> conv4<PH>(psi)) & 1u;
+  acc = (acc << 1) | ((psi >> PH) & 1u);
+  uint32_t np = (psi & ~(1u << PH)) | ((upper ^ 1u) << PH);
+  if constexpr (PH == 0) np = rotl_v<C::v>(np, P % C::v);
+  psi = np;
+}
+
+// tb_walk for four-word records: the records [lo, hs] are visited in blocks
+// of one period (phases P-1 .. 0, so every step has a compile-time phase);
+// blocks wholly inside every chain's range and not holding g_at run without
+// per-record guards.  A block's records come from the shared-memory
+// survivors or from a ring of NBUF blocks filled with cp.async.  Output bytes
+// are written once per block from the bit accumulator.
+template <class C, int T, bool SMEM, int NCH>
+__device__ __forceinline__ void tb_walk4(const KArgs& a, int64_t gslot, const uint32_t* svs, uint32_t* ring,
+                                         int L, int hs, int lo, const int (&emit_top)[NCH],
+                                         const int (&jend)[NCH], const int (&x)[NCH], const int (&nout)[NCH],
+                                         uint8_t* const (&dst)[NCH], int g_at, int (&psi)[NCH], int (&g)[NCH]) {
+  constexpr int P = Shape<C, T>::P, NBUF = tb_nbuf<C, T>();
+  static_assert(tb_kr<C, T>() == P, "one period per ring chunk");
+  uint32_t ps[NCH], acc[NCH];
+  int jmax = jend[0];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    ps[c] = (uint32_t)psi[c];
+    acc[c] = 0u;
+    g[c] = 0;
+    jmax = min(jmax, jend[c]);
+  }
+  if (hs < lo) return;
+  // block k holds records atop - k P - u, u = 0..P-1, at phases P-1-u
+  const int atop = hs + (P - 1 - (L + hs) % P);
+  const int nblk = (atop - lo) / P + 1;
+  const int64_t stride = a.surv_pairs * (int64_t)a.surv_rs;
+  int issued = 0;
+  auto issue = [&]() {
+    if constexpr (!SMEM) {
+      if (issued < nblk) {
+        uint32_t* dst0 = ring + (issued % NBUF) * (P * 4);
+        const int j0 = atop - issued * P;
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+          const int j = j0 - u;
+          if (j >= lo && j <= hs) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst0 + u * 4);
+            const uint32_t* src = a.surv + ((int64_t)j * a.surv_pairs + gslot) * a.surv_rs;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+          }
+        }
+      }
+      ++issued;
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  };
+  (void)stride;
+#pragma unroll
+  for (int q = 0; q < NBUF - 1; ++q) issue();
+  for (int k = 0; k < nblk; ++k) {
+    const int j0 = atop - k * P;
+    const uint32_t* blk;
+    int bstep;
+    if constexpr (SMEM) {
+      blk = svs + (int64_t)j0 * 4;
+      bstep = -4;
+    } else {
+      issue();
+      asm volatile("cp.async.wait_group %0;" ::"n"(NBUF - 1) : "memory");
+      blk = ring + (k % NBUF) * (P * 4);
+      bstep = 4;
+    }
+    const int jb = max(lo, j0 - P + 1);
+    const bool full = j0 <= hs && j0 - P + 1 >= lo && j0 <= jmax && (g_at > j0 || g_at < j0 - P + 1);
+    uint4 rec[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int j = j0 - u;
+      if (j >= lo && j <= hs) rec[u] = *reinterpret_cast<const uint4*>(blk + u * bstep);
+    }
+    auto step = [&](auto phc, int u, bool guarded) {
+      constexpr int PH = decltype(phc)::value;
+      const int j = j0 - u;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        if (!guarded || (j >= lo && j <= hs && j <= jend[c])) {
+          if (guarded && j == g_at) g[c] = (int)ps[c];
+          tb_step_ph<C, T, PH>(ps[c], acc[c], gather4<PH>(rec[u], x[c]));
+        }
+      }
+    };
+    auto run_block = [&](bool guarded) {
+      if constexpr (P > 5) step(std::integral_constant<int, (P > 5 ? P - 6 : 0) + 5>{}, P - 6, guarded);
+      if constexpr (P > 4) step(std::integral_constant<int, 4>{}, P - 5, guarded);
+      step(std::integral_constant<int, 3>{}, P - 4, guarded);
+      step(std::integral_constant<int, 2>{}, P - 3, guarded);
+      step(std::integral_constant<int, 1>{}, P - 2, guarded);
+      step(std::integral_constant<int, 0>{}, P - 1, guarded);
+    };
+    if (full) run_block(false); else run_block(true);
+    // the byte whose lowest record (a multiple of 8) lies in this block
+    const int m8 = (j0 >> 3) << 3;
+    if (m8 >= jb && m8 <= hs) {
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        if (m8 <= emit_top[c] && m8 <= jend[c]) {
+          const int rem = nout[c] - m8;
+          const uint32_t keep = rem >= 8 ? 0xffu : ((1u << (rem > 0 ? rem : 0)) - 1u);
+          dst[c][m8 >> 3] = (uint8_t)((acc[c] >> (m8 - jb)) & keep);
+        }
+      }
+    }
+  }
+  if constexpr (!SMEM) asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) psi[c] = (int)ps[c];
+}
+
+template <class C, int T, bool SMEM, int NCH>
+__device__ __forceinline__ void tb_walk_any(const KArgs& a, int64_t gslot, const uint32_t* svs, uint32_t* ring,
+                                            int L, int hs, int lo, const int (&emit_top)[NCH],
+                                            const int (&jend)[NCH], const int (&x)[NCH], const int (&nout)[NCH],
+                                            uint8_t* const (&dst)[NCH], int g_at, int (&psi)[NCH], int (&g)[NCH]) {
+  if constexpr (tb_period_walk<C, T>())
+    tb_walk4<C, T, SMEM, NCH>(a, gslot, svs, ring, L, hs, lo, emit_top, jend, x, nout, dst, g_at, psi, g);
+  else
+    tb_walk<C, T, SMEM, NCH>(a, gslot, svs, ring, L, hs, lo, emit_top, jend, x, nout, dst, g_at, psi, g);
+}
+
 template <class C, int T, bool SMEM>
 __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, const PbRun& gB, bool hasB, int J,
                                                int64_t gslot, uint32_t* scratch, const uint32_t* svs) {
@@ -765,7 +929,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     const int nout[2] = {gA.nout, gB.nout};
     uint8_t* const dst[2] = {gA.dst, gB.dst};
     int psi[2] = {0, 0}, g[2];
-    tb_walk<C, T, SMEM, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
+    tb_walk_any<C, T, SMEM, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
   } else {
     // Segments: lane tau walks segment s of the records of one or both PBs.
     // With BOTH, every lane walks both PBs of the pair (two chains over the
@@ -792,7 +956,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
         const int x[2] = {0, 1};
         const int nout[2] = {gA.nout, gB.nout};
         uint8_t* const dst[2] = {gA.dst, gB.dst};
-        tb_walk<C, T, SMEM, 2>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
+        tb_walk_any<C, T, SMEM, 2>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
       } else {
         const PbRun& g0 = xb ? gB : gA;
         const int emit_top[1] = {min(hi, g0.nout - 1)};
@@ -801,7 +965,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
         const int nout[1] = {g0.nout};
         uint8_t* const dst[1] = {g0.dst};
         int p1[1] = {0}, g1[1] = {0};
-        tb_walk<C, T, SMEM, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
+        tb_walk_any<C, T, SMEM, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
         psi[0] = p1[0];
         g[0] = g1[0];
       }
@@ -831,7 +995,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
             const int x[1] = {pb};
             const int nout[1] = {gp.nout};
             uint8_t* const dst[1] = {gp.dst};
-            tb_walk<C, T, SMEM, 1>(a, gslot, svs, ring, L, hi_q, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
+            tb_walk_any<C, T, SMEM, 1>(a, gslot, svs, ring, L, hi_q, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
             if (c) psi[1] = p2[0]; else psi[0] = p2[0];
           }
           ex = __shfl_sync(gmask, c ? psi[1] : psi[0], base + q, T);
