@@ -410,7 +410,6 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
     k.surv_pairs = n_slots;
     k.surv_rs = rs_max;
     k.smem_surv = 0;
-    k.one = 1u;
   }
   a.pairs = b->d_pairs;
   a.tiles = b->d_tiles;
@@ -582,7 +581,6 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   size_t cnt = 0;
   pbvd_llr_count(c, n_stages, &cnt);
   a.llr_count = (int64_t)cnt;
-  a.one = 1u;
   const int64_t grid = ceil_div(p.n_pairs, p.groups);
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
@@ -739,7 +737,6 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   size_t cnt = 0;
   pbvd_llr_count(c, n_stages, &cnt);
   a.llr_count = (int64_t)cnt;
-  a.one = 1u;
   const int64_t grid = ceil_div(p.n_pairs, p.groups);
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
@@ -918,7 +915,6 @@ int pbvd_stream_push_many(pbvd_stream* const* ss, const int8_t* const* d_llr, co
   for (size_t base = 0; base < count; base += kStreamsPerLaunch) {
     const int m = (int)std::min<size_t>(kStreamsPerLaunch, count - base);
     p.count = m;
-    p.one = 1u;
     for (int i = 0; i < m; ++i) {
       const pbvd_stream* s = ss[base + i];
       const size_t n = n_stages ? n_stages[base + i] : 0;

@@ -340,20 +340,6 @@ __device__ __forceinline__ void branch_metrics(const uint32_t (&Pk)[3], const ui
   for (int c = 0; c < C::NC; ++c) kt[c] = bm[c ^ C::g0()] + kSignBias - bm[c];
 }
 
-// Opaque constants that keep chosen additions on the FMA pipe (IMAD)
-// instead of the ALU pipe; passed in by the host so the compiler cannot fold
-// them.
-struct PipeConsts {
-  uint32_t one, minus_one;
-};
-
-__device__ __forceinline__ PipeConsts pipe_consts(const KArgs& a) {
-  PipeConsts k;
-  k.one = a.one;
-  k.minus_one = 0u - a.one;
-  return k;
-}
-
 // Byte masks of the four decisions of a butterfly: bytes 1 and 3 of t0 and
 // t1 hold the decisions in their sign bit; prmt with the sign-replicating
 // selector nibbles 9, B, D, F turns each into a 0x00 / 0xFF byte.
@@ -384,13 +370,13 @@ __device__ __forceinline__ uint32_t merge_decisions(const uint32_t* d) {
 // stores its four decision bits in survivor word b / BPW at bits q (PB A of
 // k0), 8 + q (PB B of k0), 16 + q (PB A of k1), 24 + q (PB B of k1),
 // q = b % BPW; a set bit means the upper branch was kept.
-// Per butterfly: two fused add-min (ALU), two candidate adds (FMA), one
-// decision difference on each pipe, one byte permute and 7/8 of a select
-// (ALU) for the decision bits.
+// Per butterfly: two fused 16x2 add-min, two candidate adds, two
+// three-input decision differences, one byte permute and 7/8 of a select for
+// the decision bits (the compiler spreads the adds over the ALU and FMA
+// pipes).
 template <class C, int T, int PH>
 __device__ __forceinline__ void acs_stage(uint32_t (&pm)[Shape<C, T>::M], uint32_t (&wd)[Shape<C, T>::W],
-                                          const uint32_t (&bm)[C::NC], const uint32_t (&kt)[C::NC],
-                                          const PipeConsts& pc) {
+                                          const uint32_t (&bm)[C::NC], const uint32_t (&kt)[C::NC]) {
   using S = Shape<C, T>;
   constexpr uint32_t g0 = C::g0(), gK = C::gK();
 #pragma unroll
@@ -404,10 +390,10 @@ __device__ __forceinline__ void acs_stage(uint32_t (&pm)[Shape<C, T>::M], uint32
       const uint32_t al = C::alpha(rotr_v<C::v>((uint32_t)k0, PH));
       const uint32_t be = al ^ gK;
       const uint32_t X = pm[k0], Y = pm[k1];
-      const uint32_t c1 = Y * pc.one + bm[al ^ g0];
-      const uint32_t c3 = Y * pc.one + bm[be ^ g0];
+      const uint32_t c1 = Y + bm[al ^ g0];
+      const uint32_t c3 = Y + bm[be ^ g0];
       const uint32_t t0 = Y + kt[al] - X;
-      const uint32_t t1 = X * pc.minus_one + (Y * pc.one + kt[be]);
+      const uint32_t t1 = Y + kt[be] - X;
       pm[k0] = __viaddmin_s16x2(X, bm[al], c1);
       pm[k1] = __viaddmin_s16x2(X, bm[be], c3);
       d[q] = decision_bytes(t0, t1);
@@ -468,8 +454,7 @@ template <class C, int T, bool CHECKED, bool PUNCT, bool SMEM, bool STORE>
 __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], const uint32_t (&sel)[Shape<C, T>::P][3],
                                                const KArgs& a, const int8_t* bufA, int cbA, const int8_t* bufB,
                                                int cbB, bool hasB, int i0, int I, int L, int tau, PbRun& gA,
-                                               PbRun& gB, uint32_t*& gsv, int64_t rec_stride, uint32_t*& ssv,
-                                               const PipeConsts& pc) {
+                                               PbRun& gB, uint32_t*& gsv, int64_t rec_stride, uint32_t*& ssv) {
   using S = Shape<C, T>;
   constexpr int W = S::W;
   constexpr int R = C::R;
@@ -517,14 +502,14 @@ __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], c
     branch_metrics<C, (T > 1)>(Pk, sel[ph], bm, kt);
     uint32_t wd[W];
     // ph is a compile-time constant after unrolling
-    if constexpr (S::P > 0) if (ph == 0) acs_stage<C, T, 0>(pm, wd, bm, kt, pc);
-    if constexpr (S::P > 1) if (ph == 1) acs_stage<C, T, (S::P > 1 ? 1 : 0)>(pm, wd, bm, kt, pc);
-    if constexpr (S::P > 2) if (ph == 2) acs_stage<C, T, (S::P > 2 ? 2 : 0)>(pm, wd, bm, kt, pc);
-    if constexpr (S::P > 3) if (ph == 3) acs_stage<C, T, (S::P > 3 ? 3 : 0)>(pm, wd, bm, kt, pc);
-    if constexpr (S::P > 4) if (ph == 4) acs_stage<C, T, (S::P > 4 ? 4 : 0)>(pm, wd, bm, kt, pc);
-    if constexpr (S::P > 5) if (ph == 5) acs_stage<C, T, (S::P > 5 ? 5 : 0)>(pm, wd, bm, kt, pc);
-    if constexpr (S::P > 6) if (ph == 6) acs_stage<C, T, (S::P > 6 ? 6 : 0)>(pm, wd, bm, kt, pc);
-    if constexpr (S::P > 7) if (ph == 7) acs_stage<C, T, (S::P > 7 ? 7 : 0)>(pm, wd, bm, kt, pc);
+    if constexpr (S::P > 0) if (ph == 0) acs_stage<C, T, 0>(pm, wd, bm, kt);
+    if constexpr (S::P > 1) if (ph == 1) acs_stage<C, T, (S::P > 1 ? 1 : 0)>(pm, wd, bm, kt);
+    if constexpr (S::P > 2) if (ph == 2) acs_stage<C, T, (S::P > 2 ? 2 : 0)>(pm, wd, bm, kt);
+    if constexpr (S::P > 3) if (ph == 3) acs_stage<C, T, (S::P > 3 ? 3 : 0)>(pm, wd, bm, kt);
+    if constexpr (S::P > 4) if (ph == 4) acs_stage<C, T, (S::P > 4 ? 4 : 0)>(pm, wd, bm, kt);
+    if constexpr (S::P > 5) if (ph == 5) acs_stage<C, T, (S::P > 5 ? 5 : 0)>(pm, wd, bm, kt);
+    if constexpr (S::P > 6) if (ph == 6) acs_stage<C, T, (S::P > 6 ? 6 : 0)>(pm, wd, bm, kt);
+    if constexpr (S::P > 7) if (ph == 7) acs_stage<C, T, (S::P > 7 ? 7 : 0)>(pm, wd, bm, kt);
     if (CHECKED ? (i >= L) : STORE) {
       if constexpr (SMEM) {
 #pragma unroll
@@ -1057,7 +1042,6 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   uint32_t* gsv = a.surv + gslot * a.surv_rs + tau * S::W;
   uint32_t* ssv = svs + tau * S::W;
 
-  const PipeConsts pc = pipe_consts(a);
   int since_renorm = 0;
   for (int i0 = 0; i0 < I; i0 += P) {
     if (i0 % CH == 0) {
@@ -1082,13 +1066,13 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
     const bool fast = i0 >= fast_lo && i0 <= fast_hi;
     if (fast && i0 >= L)
       forward_period<C, T, false, PUNCT, SMEM, true>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
-                                                     gB, gsv, rec_stride, ssv, pc);
+                                                     gB, gsv, rec_stride, ssv);
     else if (fast && i0 + P <= L)
       forward_period<C, T, false, PUNCT, SMEM, false>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
-                                                      gB, gsv, rec_stride, ssv, pc);
+                                                      gB, gsv, rec_stride, ssv);
     else
       forward_period<C, T, true, PUNCT, SMEM, true>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
-                                                    gB, gsv, rec_stride, ssv, pc);
+                                                    gB, gsv, rec_stride, ssv);
     if (i0 + P < I) {
       // end of a full period: transpose back to psi = u (T > 1)
       if constexpr (vector_transpose<C, T>()) {

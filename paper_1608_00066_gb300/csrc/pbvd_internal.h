@@ -24,7 +24,6 @@ struct KArgs {
   int32_t punct_P;        // 0: not punctured, else pattern period
   int32_t punct_C;        // values sent per period
   int64_t llr_count;      // soft values readable at llr
-  uint32_t one;           // the value 1, opaque to the compiler (pipe balancing)
   int16_t punct_off[32 * 4];  // [col][r]: offset in the period, -1 = punctured
   int16_t punct_pre[33];      // values sent in the columns before col
 };
@@ -96,7 +95,6 @@ struct StreamDev {
 constexpr int kStreamsPerLaunch = 128;
 struct StreamLaunch {
   int32_t count;
-  uint32_t one;          // 1, opaque to the compiler
   StreamDev d[kStreamsPerLaunch];
 };
 

@@ -127,7 +127,7 @@ __device__ __forceinline__ void stream_walk(const StreamDev& sd, int64_t start, 
 }
 
 template <class C, int T>
-__device__ __forceinline__ void stream_push(const StreamDev& sd, uint32_t one, uint32_t* smem) {
+__device__ __forceinline__ void stream_push(const StreamDev& sd, uint32_t* smem) {
   using S = Shape<C, T>;
   using SS = StreamSmem<C, T>;
   constexpr int R = C::R, M = S::M, P = S::P, W = S::W, RW = S::RW, SC = SS::SC, CB = SS::CB;
@@ -151,9 +151,6 @@ __device__ __forceinline__ void stream_push(const StreamDev& sd, uint32_t one, u
 #pragma unroll
     for (int q = 0; q < 3; ++q) sel[ph][q] = 0u - ((m >> (R - 1 - q)) & 1u);
   }
-  PipeConsts pc;
-  pc.one = one;
-  pc.minus_one = 0u - one;
 
   // chunk c holds stages [c SC, (c + 1) SC) of the push; stage i >= ncarry
   // is new stage i - ncarry of the caller's buffer
@@ -191,14 +188,14 @@ __device__ __forceinline__ void stream_push(const StreamDev& sd, uint32_t one, u
       for (int q = 0; q < 3; ++q) Pk[q] = q < R ? pack_soft((uint32_t)(uint8_t)src[q], 0u) : 0u;
       uint32_t bm[C::NC], kt[C::NC], wd[W];
       branch_metrics<C, (T > 1)>(Pk, sel[ph], bm, kt);
-      if (ph == 0) acs_stage<C, T, 0>(pm, wd, bm, kt, pc);
-      if constexpr (P > 1) if (ph == 1) acs_stage<C, T, (P > 1 ? 1 : 0)>(pm, wd, bm, kt, pc);
-      if constexpr (P > 2) if (ph == 2) acs_stage<C, T, (P > 2 ? 2 : 0)>(pm, wd, bm, kt, pc);
-      if constexpr (P > 3) if (ph == 3) acs_stage<C, T, (P > 3 ? 3 : 0)>(pm, wd, bm, kt, pc);
-      if constexpr (P > 4) if (ph == 4) acs_stage<C, T, (P > 4 ? 4 : 0)>(pm, wd, bm, kt, pc);
-      if constexpr (P > 5) if (ph == 5) acs_stage<C, T, (P > 5 ? 5 : 0)>(pm, wd, bm, kt, pc);
-      if constexpr (P > 6) if (ph == 6) acs_stage<C, T, (P > 6 ? 6 : 0)>(pm, wd, bm, kt, pc);
-      if constexpr (P > 7) if (ph == 7) acs_stage<C, T, (P > 7 ? 7 : 0)>(pm, wd, bm, kt, pc);
+      if (ph == 0) acs_stage<C, T, 0>(pm, wd, bm, kt);
+      if constexpr (P > 1) if (ph == 1) acs_stage<C, T, (P > 1 ? 1 : 0)>(pm, wd, bm, kt);
+      if constexpr (P > 2) if (ph == 2) acs_stage<C, T, (P > 2 ? 2 : 0)>(pm, wd, bm, kt);
+      if constexpr (P > 3) if (ph == 3) acs_stage<C, T, (P > 3 ? 3 : 0)>(pm, wd, bm, kt);
+      if constexpr (P > 4) if (ph == 4) acs_stage<C, T, (P > 4 ? 4 : 0)>(pm, wd, bm, kt);
+      if constexpr (P > 5) if (ph == 5) acs_stage<C, T, (P > 5 ? 5 : 0)>(pm, wd, bm, kt);
+      if constexpr (P > 6) if (ph == 6) acs_stage<C, T, (P > 6 ? 6 : 0)>(pm, wd, bm, kt);
+      if constexpr (P > 7) if (ph == 7) acs_stage<C, T, (P > 7 ? 7 : 0)>(pm, wd, bm, kt);
       uint32_t* rec = sd.ring + (int64_t)rpos * RW + tau * W;
       rpos = rpos + 1 == H ? 0 : rpos + 1;
 #pragma unroll
@@ -264,7 +261,7 @@ __global__ void __launch_bounds__(kStreamCta) pbvd_stream_kernel(const __grid_co
   const int g = threadIdx.x / T;
   const int idx = blockIdx.x * (kStreamCta / T) + g;
   if (idx >= p.count) return;
-  stream_push<C, T>(p.d[idx], p.one, smem + g * StreamSmem<C, T>::WORDS);
+  stream_push<C, T>(p.d[idx], smem + g * StreamSmem<C, T>::WORDS);
 }
 
 using K7 = Code<7, 0171u, 0133u, 0u>;
