@@ -50,6 +50,24 @@ def algorithmic_ops_per_bit(N: int, D: int, L: int) -> float:
     return 3.0 * N * (D + 2 * L) / D
 
 
+# DRAM bytes (read + write) of one launch of the stream decode kernel, from
+# the ncu capture summarised in profiles/pbvd_decode_k7_stream_2e24.md, keyed
+# by kernel configuration (threads per pair, CTA threads, survivors in
+# shared memory).  Reported only when the timed launch used that
+# configuration; a change to the kernel invalidates it.
+PROFILED_TRAFFIC = {(4, 32, 0): 123738624 + 127635456}
+
+
+def hbm_peak_gbs() -> tuple:
+    """Measured copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else
+    the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 def peak_int16_ops(sm_count: int = 152, clock_hz: float = 2.07e9) -> float:
     """Issue-limited integer peak: 4 schedulers x 32 lanes per SM per clock,
     two 16-bit operations per lane (packed 16x2 arithmetic)."""
@@ -298,6 +316,10 @@ def run_ours(args, rank: int, world: int):
     ops = algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP) * K_INFO
     peak = peak_int16_ops()
     achieved = ops / (ms * 1e-3)
+    key = (cfg["threads_per_pair"], cfg["cta_threads"], cfg["survivors_in_smem"])
+    traffic = args.traffic if args.traffic is not None else PROFILED_TRAFFIC.get(key)
+    hbm_peak, hbm_src = hbm_peak_gbs()
+    alg_bytes = int(frame.llr.nbytes) + nbytes
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -309,7 +331,11 @@ def run_ours(args, rank: int, world: int):
         "roofline": {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(peak / 1e12, 3),
                      "unit": "Tops/s (int16)", "frac": round(achieved / peak, 4),
                      "ops_per_bit": round(algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP), 2),
-                     "traffic": args.traffic},
+                     "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "peak_source": "issue limit: 152 SMs x 4 schedulers x 32 lanes x 2 (16x2) x 2.07 GHz"},
+        "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / (ms * 1e-3) / 1e9, 1),
+                         "peak": hbm_peak, "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                         "algorithmic_bytes": alg_bytes, "peak_source": hbm_src},
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(frame.llr.nbytes),
                 "d2h_bytes_per_step": int(nbytes)},
         "gpu_launches": args.steps,
