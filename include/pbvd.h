@@ -101,6 +101,32 @@ PBVD_API void pbvd_destroy(pbvd_ctx *ctx);
 PBVD_API int pbvd_decode(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
                 uint8_t *d_out, void *stream);
 
+/* Decodes a stream held in HOST memory, overlapping the host-device copies
+ * with the decoding, after the multi-stream pipeline of Sec. IV-C (Eq. (7)):
+ * the stream's blocks are cut into `segments` runs of whole pairs of blocks
+ * (0 = automatic: up to 8 runs of at least 1024 blocks; at most 64); the soft
+ * values of each run go host -> device in order on one copy stream, each run
+ * is decoded on one of sixteen compute streams as soon as its own values and
+ * those of the next run (its last block reads L stages beyond the run) have
+ * arrived, and its packed bits go device -> host on the same compute stream.
+ * Runs decode concurrently, so the GPU fills up while later runs are still
+ * being copied.
+ *   h_llr      host soft values, laid out as d_llr of pbvd_decode; page-locked
+ *              memory is needed for the copies to overlap (pageable memory
+ *              works but is copied synchronously by the driver)
+ *   h_out      host, ceil(n_stages / 8) bytes, written as d_out of pbvd_decode
+ *   stream     the caller's stream: the work starts after what is already
+ *              queued on it, and work queued on it later waits for the whole
+ *              decode, so h_out is complete once the stream reaches that point
+ * The bits are exactly those of pbvd_decode with the same context.  Uses the
+ * context's configuration with survivors in global memory; the context owns
+ * the device copies of the stream, its copy and compute streams and events,
+ * grown on first use of a larger size (device allocations that synchronise).
+ * Host buffers must stay valid until the stream has passed the call; calls
+ * on one context must not overlap on the GPU. */
+PBVD_API int pbvd_decode_host(pbvd_ctx *ctx, const int8_t *h_llr, size_t n_stages,
+                              uint8_t *h_out, int segments, void *stream);
+
 /* Number of soft values d_llr must hold for n_stages stages. */
 PBVD_API int pbvd_llr_count(const pbvd_ctx *ctx, size_t n_stages, size_t *count);
 

@@ -102,6 +102,19 @@ struct pbvd_ctx {
   void* work;
   size_t work_bytes;
   pbvd_batch* batch;  // work list of the last pbvd_decode_batch led by this context
+  // pbvd_decode_host: copy stream, compute lanes, events and device buffers
+  int hp_ready;
+  cudaStream_t hp_copy;
+  cudaStream_t hp_lane[16];
+  cudaEvent_t hp_fork;
+  cudaEvent_t hp_in[64];
+  cudaEvent_t hp_done[16];
+  int8_t* hp_llr;
+  size_t hp_llr_cap;
+  uint8_t* hp_out;
+  size_t hp_out_cap;
+  uint32_t* hp_surv;
+  size_t hp_surv_cap;
 };
 
 namespace {
@@ -189,6 +202,67 @@ int grant_smem(int entry, bool smem_surv, size_t bytes) {
   if ((int)bytes <= reg.smem_set[slot]) return PBVD_OK;
   PBVD_CUDA(reg.entries[entry].set_max_smem[smem_surv ? 1 : 0]((int)bytes));
   reg.smem_set[slot] = (int)bytes;
+  return PBVD_OK;
+}
+
+}  // namespace
+
+
+// ------------------------------------------------- host-memory pipeline --
+
+namespace {
+
+constexpr int kHostLanes = 16;
+constexpr int kHostMaxSegments = 64;
+
+void host_pipeline_release(pbvd_ctx* c) {
+  if (c->hp_ready) {
+    cudaStreamDestroy(c->hp_copy);
+    for (int l = 0; l < kHostLanes; ++l) {
+      cudaStreamDestroy(c->hp_lane[l]);
+      cudaEventDestroy(c->hp_done[l]);
+    }
+    cudaEventDestroy(c->hp_fork);
+    for (int i = 0; i < kHostMaxSegments; ++i) cudaEventDestroy(c->hp_in[i]);
+    c->hp_ready = 0;
+  }
+  if (c->hp_llr) cudaFree(c->hp_llr);
+  if (c->hp_out) cudaFree(c->hp_out);
+  if (c->hp_surv) cudaFree(c->hp_surv);
+  c->hp_llr = nullptr;
+  c->hp_out = nullptr;
+  c->hp_surv = nullptr;
+  c->hp_llr_cap = c->hp_out_cap = c->hp_surv_cap = 0;
+}
+
+int host_pipeline_setup(pbvd_ctx* c) {
+  if (c->hp_ready) return PBVD_OK;
+  PBVD_CUDA(cudaStreamCreateWithFlags(&c->hp_copy, cudaStreamNonBlocking));
+  for (int l = 0; l < kHostLanes; ++l) {
+    PBVD_CUDA(cudaStreamCreateWithFlags(&c->hp_lane[l], cudaStreamNonBlocking));
+    PBVD_CUDA(cudaEventCreateWithFlags(&c->hp_done[l], cudaEventDisableTiming));
+  }
+  PBVD_CUDA(cudaEventCreateWithFlags(&c->hp_fork, cudaEventDisableTiming));
+  for (int i = 0; i < kHostMaxSegments; ++i) PBVD_CUDA(cudaEventCreateWithFlags(&c->hp_in[i], cudaEventDisableTiming));
+  c->hp_ready = 1;
+  return PBVD_OK;
+}
+
+template <class T>
+int grow_device(T** p, size_t* cap, size_t bytes) {
+  if (bytes <= *cap && *p) return PBVD_OK;
+  if (*p) {
+    cudaError_t e = cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e);
+  }
+  *cap = bytes;
   return PBVD_OK;
 }
 
@@ -504,10 +578,9 @@ int pbvd_create(pbvd_ctx** out, int K, int R, const uint32_t* gens, const uint8_
 void pbvd_destroy(pbvd_ctx* c) {
   if (!c) return;
   if (c->batch) pbvd_batch_destroy(c->batch);
-  if (c->work) {
-    cudaDeviceSynchronize();
-    cudaFree(c->work);
-  }
+  if (c->work || c->hp_ready) cudaDeviceSynchronize();
+  if (c->work) cudaFree(c->work);
+  host_pipeline_release(c);
   delete c;
 }
 
@@ -585,6 +658,100 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
   PBVD_CUDA(e.launch[p.smem_surv ? 1 : 0](a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
+  return PBVD_OK;
+}
+
+int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t* h_out, int segments,
+                     void* stream) {
+  if (!c || !h_llr || !h_out || n_stages == 0 || segments < 0) return PBVD_EINVAL;
+  if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
+  int dev = -1;
+  PBVD_CUDA(cudaGetDevice(&dev));
+  if (dev != c->device) return PBVD_EINVAL;
+  // the kernel configuration pbvd_decode would use, survivors in global
+  // memory (one workspace slice per compute lane)
+  pbvd_ctx cc = *c;
+  cc.cfg.survivors_in_smem = 0;
+  Plan p;
+  int rc = plan_decode(&cc, n_stages, &p);
+  if (rc != PBVD_OK) return rc;
+  const int64_t nb = p.n_blocks;
+  // automatic: up to 8 runs of at least 1024 blocks (more, shorter runs
+  // start their decode sooner but each kernel of a run then underfills the
+  // GPU; 8 was the fastest for a 2^24-stage stream)
+  int S = segments > 0 ? segments : (int)std::max<int64_t>(1, std::min<int64_t>(8, nb / 1024));
+  S = (int)std::min<int64_t>(std::min<int64_t>(S, kHostMaxSegments), nb);
+  int64_t bps = ceil_div(nb, S);
+  bps += bps & 1;  // whole pairs per segment
+  S = (int)ceil_div(nb, bps);
+  const KernelEntry& e = registry().entries[p.entry];
+  const int64_t jmax = (int64_t)c->D + c->L;
+  const size_t slice_words = (size_t)jmax * (size_t)(bps / 2) * e.words_per_stage;
+  size_t llr_bytes = 0;
+  pbvd_llr_count(c, n_stages, &llr_bytes);
+  const size_t out_bytes = (n_stages + 7) / 8;
+  rc = host_pipeline_setup(c);
+  if (rc != PBVD_OK) return rc;
+  rc = grow_device(&c->hp_llr, &c->hp_llr_cap, llr_bytes);
+  if (rc != PBVD_OK) return rc;
+  rc = grow_device(&c->hp_out, &c->hp_out_cap, out_bytes);
+  if (rc != PBVD_OK) return rc;
+  rc = grow_device(&c->hp_surv, &c->hp_surv_cap, (size_t)kHostLanes * slice_words * 4);
+  if (rc != PBVD_OK) return rc;
+  rc = grant_smem(p.entry, false, p.smem_bytes);
+  if (rc != PBVD_OK) return rc;
+
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  PBVD_CUDA(cudaEventRecord(c->hp_fork, user));
+  PBVD_CUDA(cudaStreamWaitEvent(c->hp_copy, c->hp_fork, 0));
+  for (int l = 0; l < kHostLanes; ++l) PBVD_CUDA(cudaStreamWaitEvent(c->hp_lane[l], c->hp_fork, 0));
+  // soft values of segment i's own blocks, in order on one copy stream
+  for (int i = 0; i < S; ++i) {
+    const size_t s0 = (size_t)(i * bps * c->D);
+    const size_t s1 = std::min(n_stages, (size_t)((i + 1) * bps * c->D));
+    size_t v0 = 0, v1 = 0;
+    pbvd_llr_count(c, s0, &v0);
+    pbvd_llr_count(c, s1, &v1);
+    if (v1 > v0)
+      PBVD_CUDA(cudaMemcpyAsync(c->hp_llr + v0, h_llr + v0, v1 - v0, cudaMemcpyHostToDevice, c->hp_copy));
+    PBVD_CUDA(cudaEventRecord(c->hp_in[i], c->hp_copy));
+  }
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.llr = c->hp_llr;
+  a.out = c->hp_out;
+  a.n = (int64_t)n_stages;
+  a.surv_rs = e.words_per_stage;
+  a.D = c->D;
+  a.L = c->L;
+  a.smem_surv = 0;
+  a.smem_rec_words = 0;
+  a.punct_P = c->P;
+  a.punct_C = c->punct_C;
+  std::memcpy(a.punct_off, c->punct_off, sizeof(a.punct_off));
+  std::memcpy(a.punct_pre, c->punct_pre, sizeof(a.punct_pre));
+  a.llr_count = (int64_t)llr_bytes;
+  for (int i = 0; i < S; ++i) {
+    const int l = i % kHostLanes;
+    cudaStream_t st = c->hp_lane[l];
+    // a block reads L stages beyond its segment: wait for the next copy too
+    PBVD_CUDA(cudaStreamWaitEvent(st, c->hp_in[std::min(i + 1, S - 1)], 0));
+    const int64_t b0 = (int64_t)i * bps, b1 = std::min<int64_t>(nb, b0 + bps);
+    a.b_first = b0;
+    a.n_blocks = b1;
+    a.n_pairs = ceil_div(b1 - b0, 2);
+    a.surv = c->hp_surv + (size_t)l * slice_words;
+    a.surv_pairs = a.n_pairs;
+    const int64_t grid = ceil_div(a.n_pairs, p.groups);
+    PBVD_CUDA(e.launch[0](a, (int)grid, p.cta, p.smem_bytes, st));
+    const size_t o0 = (size_t)(b0 * c->D / 8);
+    const size_t o1 = (std::min(n_stages, (size_t)(b1 * c->D)) + 7) / 8;
+    PBVD_CUDA(cudaMemcpyAsync(h_out + o0, c->hp_out + o0, o1 - o0, cudaMemcpyDeviceToHost, st));
+  }
+  for (int l = 0; l < kHostLanes; ++l) {
+    PBVD_CUDA(cudaEventRecord(c->hp_done[l], c->hp_lane[l]));
+    PBVD_CUDA(cudaStreamWaitEvent(user, c->hp_done[l], 0));
+  }
   return PBVD_OK;
 }
 

@@ -1128,8 +1128,9 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   traceback_pair<C, T, SMEM>(a, gA, gB, wk.hasB, J, gslot, scratch, svs);
 }
 
-// Plain launch: pair p of one stream.  SMEM: survivor records of each group
-// in shared memory (a.smem_rec_words words per group), else in a.surv.
+// Plain launch: pair p of blocks [b_first, n_blocks) of one stream.  SMEM:
+// survivor records of each group in shared memory (a.smem_rec_words words
+// per group), else in a.surv.
 template <class C, int T, bool PUNCT, bool SMEM>
 __global__ void __launch_bounds__(256, 1) pbvd_decode_kernel(const KArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -1145,10 +1146,10 @@ __global__ void __launch_bounds__(256, 1) pbvd_decode_kernel(const KArgs a) {
   wk.A.llr_end = a.llr + a.llr_count;
   wk.A.out = a.out;
   wk.A.n = a.n;
-  wk.A.b = 2 * pair;
+  wk.A.b = a.b_first + 2 * pair;
   wk.B = wk.A;
-  wk.B.b = 2 * pair + 1;
-  wk.hasB = (2 * pair + 1) < a.n_blocks;
+  wk.B.b = wk.A.b + 1;
+  wk.hasB = wk.B.b < a.n_blocks;
   decode_pair<C, T, PUNCT, SMEM>(a, wk, pair, scratch, svs);
 }
 

@@ -13,8 +13,9 @@ struct KArgs {
   uint8_t* out;           // packed decoded bits
   uint32_t* surv;         // global survivor records, [J][surv_pairs][surv_rs] words
   int64_t n;              // stages of the stream
-  int64_t n_blocks;       // ceil(n / D)
-  int64_t n_pairs;        // ceil(n_blocks / 2)
+  int64_t b_first;        // first block of this launch
+  int64_t n_blocks;       // end (exclusive) of this launch's blocks; ceil(n / D) for a whole stream
+  int64_t n_pairs;        // ceil((n_blocks - b_first) / 2)
   int64_t surv_pairs;     // pair slots per record row of surv
   int32_t surv_rs;        // words per record slot (>= the code's T*W record)
   int32_t pad_rs;

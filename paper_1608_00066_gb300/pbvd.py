@@ -35,7 +35,7 @@ EXPORTS = (
     "pbvd_decode_noalloc", "pbvd_noalloc_max_survivor_bytes",
     "pbvd_batch_prepare", "pbvd_batch_run", "pbvd_batch_destroy", "pbvd_autotune",
     "pbvd_stream_open", "pbvd_stream_push", "pbvd_stream_push_many", "pbvd_stream_close",
-    "pbvd_stream_released", "pbvd_stream_destroy", "pbvd_batch_update",
+    "pbvd_stream_released", "pbvd_stream_destroy", "pbvd_batch_update", "pbvd_decode_host",
 )
 
 
@@ -85,6 +85,8 @@ def load(path: Optional[str] = None):
         lib.pbvd_destroy.restype = None
         lib.pbvd_decode.argtypes = [V, V, SZ, V, V]
         lib.pbvd_decode.restype = I
+        lib.pbvd_decode_host.argtypes = [V, V, SZ, V, I, V]
+        lib.pbvd_decode_host.restype = I
         lib.pbvd_llr_count.argtypes = [V, SZ, ctypes.POINTER(SZ)]
         lib.pbvd_llr_count.restype = I
         lib.pbvd_decode_batch.argtypes = [V, SZ, V]
@@ -161,6 +163,12 @@ def pbvd_destroy(ctx: int) -> None:
 
 def pbvd_decode(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0) -> None:
     _check(load().pbvd_decode(ctx, d_llr, n_stages, d_out, stream or None), "pbvd_decode")
+
+
+def pbvd_decode_host(ctx: int, h_llr: int, n_stages: int, h_out: int, segments: int = 0, stream: int = 0) -> None:
+    """Host-memory decode with the copies overlapped with decoding (host
+    pointers; page-locked memory for the overlap)."""
+    _check(load().pbvd_decode_host(ctx, h_llr, n_stages, h_out, segments, stream), "pbvd_decode_host")
 
 
 def pbvd_decode_noalloc(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0) -> None:
@@ -338,6 +346,25 @@ class Decoder:
             raise ValueError("out must be a uint8 CUDA tensor of %d bytes" % nbytes)
         s = stream if stream is not None else torch.cuda.current_stream(llr.device)
         pbvd_decode(self.ctx, llr.data_ptr(), n_stages, out.data_ptr(), s.cuda_stream)
+        return out
+
+
+    def decode_host(self, llr, n_stages: int, out=None, segments: int = 0, stream=None):
+        """llr: int8 CPU tensor (page-locked for overlap) of the sent soft
+        values; returns (or fills) a uint8 CPU tensor of ceil(n_stages / 8)
+        packed bytes, complete once ``stream`` has passed this call."""
+        import torch
+        if llr.dtype != torch.int8 or llr.is_cuda or not llr.is_contiguous():
+            raise ValueError("llr must be a contiguous int8 CPU tensor")
+        if llr.numel() < self.llr_count(n_stages):
+            raise ValueError("llr holds %d values, %d needed" % (llr.numel(), self.llr_count(n_stages)))
+        nbytes = (n_stages + 7) // 8
+        if out is None:
+            out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        elif out.numel() < nbytes or out.dtype != torch.uint8 or out.is_cuda or not out.is_contiguous():
+            raise ValueError("out must be a contiguous uint8 CPU tensor of %d bytes" % nbytes)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        pbvd_decode_host(self.ctx, llr.data_ptr(), n_stages, out.data_ptr(), segments, s.cuda_stream)
         return out
 
 

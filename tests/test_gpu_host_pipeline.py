@@ -1,0 +1,80 @@
+"""pbvd_decode_host: a stream in host memory, cut into runs of blocks whose
+copies overlap the decoding (Sec. IV-C), must give exactly the bits of
+pbvd_decode on the same soft values (and so the block oracle's), for any
+number of runs, ragged last runs, punctured codes, the 256-state code,
+page-locked and pageable host buffers, and calls in a row."""
+import numpy as np
+import pytest
+
+from paper_1608_00066_gb300 import pbvd, synth
+
+from gpu_util import make_decoder, oracle_bits
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1608_00066_gb300 import build
+    build.build()
+    pbvd.load()
+
+
+def _device_bits(dec, f):
+    d = torch.from_numpy(f.llr).cuda()
+    out = dec.decode(d, f.n_stages)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _host_bits(dec, f, segments, pinned=True):
+    h = torch.from_numpy(f.llr.copy())
+    if pinned:
+        h = h.pin_memory()
+    nbytes = (f.n_stages + 7) // 8
+    out = torch.full((nbytes,), 0xA5, dtype=torch.uint8)
+    if pinned:
+        out = out.pin_memory()
+    dec.decode_host(h, f.n_stages, out=out, segments=segments)
+    torch.cuda.synchronize()
+    return out.numpy().copy()
+
+
+@pytest.mark.parametrize("name,k,D,L", [
+    ("K7_r1/2", 300000, 512, 42),
+    ("K7_r1/2", 123457, 256, 35),
+    ("K7_r3/4", 200001, 512, 42),
+    ("K9_r1/3", 100003, 1024, 64),
+])
+def test_matches_device_decode(name, k, D, L):
+    spec = synth.CODES[name]
+    f = synth.make_frame(spec, k, 2.0, seed=k)
+    dec = make_decoder(spec, D, L)
+    want = _device_bits(dec, f)
+    for segments in (0, 1, 2, 3, 7, 64):
+        got = _host_bits(dec, f, segments)
+        assert np.array_equal(got, want), segments
+    dec.close()
+
+
+def test_small_and_ragged_against_oracle():
+    spec = synth.K7_R12
+    for k, D, L, segments in ((1, 8, 5, 0), (50, 16, 20, 3), (3001, 64, 42, 64), (4000, 512, 42, 5)):
+        f = synth.make_frame(spec, k, 1.5, seed=100 + k)
+        dec = make_decoder(spec, D, L)
+        want = np.packbits(oracle_bits(spec, f.llr, f.n_stages, D, L), bitorder="little")
+        got = _host_bits(dec, f, segments)
+        assert np.array_equal(got, want), (k, D, L, segments)
+        dec.close()
+
+
+def test_pageable_buffers_and_calls_in_a_row():
+    spec = synth.K7_R12
+    dec = make_decoder(spec, 512, 42)
+    frames = [synth.make_frame(spec, k, 2.5, seed=k) for k in (250000, 70001, 250000)]
+    for f in frames:
+        want = _device_bits(dec, f)
+        assert np.array_equal(_host_bits(dec, f, 0, pinned=False), want)
+        assert np.array_equal(_host_bits(dec, f, 6, pinned=True), want)
+    dec.close()
