@@ -295,14 +295,19 @@ __device__ __forceinline__ void read_raw(const KArgs& a, PbRun& g, const int8_t*
   }
 }
 
-// Packs the raw bytes of PB A (low lane) and PB B (high lane) into
-// 127 + max(lambda, -127) per lane: byte ^ 0x80 = lambda + 128, clamped to at
-// least 1, minus 1.
+// 127 + max(lambda, -127) per 16-bit lane from sign-extended soft values:
+// max(lambda + 127, 0) in one fused add-max (lambda = -128 gives 0).
+__device__ __forceinline__ uint32_t soft_lanes(uint32_t x) {
+  return __viaddmax_s16x2_relu(x, 0x007F007Fu, 0u);
+}
+
+// Packs the raw soft-value bytes of PB A (low lane) and PB B (high lane):
+// byte permute with sign replication (selector nibbles 8 and C copy the sign
+// of bytes 0 and 4) into two sign-extended 16-bit lanes, then soft_lanes.
 __device__ __forceinline__ uint32_t pack_soft(uint32_t ua, uint32_t ub) {
   uint32_t x;
-  asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(x) : "r"(ua), "r"(ub));
-  x = __vmaxu2(x ^ 0x00800080u, 0x00010001u);
-  return x - 0x00010001u;
+  asm("prmt.b32 %0, %1, %2, 0xC480;" : "=r"(x) : "r"(ua), "r"(ub));
+  return soft_lanes(x);
 }
 
 // ------------------------------------------------------------ ACS stage --
@@ -329,15 +334,33 @@ __device__ __forceinline__ void branch_metrics(const uint32_t (&Pk)[3], const ui
       Mp[q] = m0;
     }
   }
+  constexpr uint32_t FULL = (uint32_t)C::NC - 1u;
+  if constexpr (C::g0() == FULL) {
+    // every generator taps the oldest cell, so BM(c ^ g0) = 254 R - BM(c):
+    // half the sums, the other half by complement, and kt[c] =
+    // 254 R + 0x8000 - 2 BM(c) per lane (no borrow between the lanes)
+    constexpr uint32_t SUM = (uint32_t)(254 * R) * 0x00010001u;
 #pragma unroll
-  for (int c = 0; c < C::NC; ++c) {
-    uint32_t s = 0;
+    for (int c = 0; c < C::NC / 2; ++c) {
+      uint32_t s = 0;
 #pragma unroll
-    for (int q = 0; q < R; ++q) s += ((c >> (R - 1 - q)) & 1) ? Pp[q] : Mp[q];
-    bm[c] = s;
+      for (int q = 0; q < R; ++q) s += ((c >> (R - 1 - q)) & 1) ? Pp[q] : Mp[q];
+      bm[c] = s;
+      bm[c ^ FULL] = SUM - s;
+    }
+#pragma unroll
+    for (int c = 0; c < C::NC; ++c) kt[c] = (SUM + kSignBias) - 2u * bm[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < C::NC; ++c) {
+      uint32_t s = 0;
+#pragma unroll
+      for (int q = 0; q < R; ++q) s += ((c >> (R - 1 - q)) & 1) ? Pp[q] : Mp[q];
+      bm[c] = s;
+    }
+#pragma unroll
+    for (int c = 0; c < C::NC; ++c) kt[c] = bm[c ^ C::g0()] + kSignBias - bm[c];
   }
-#pragma unroll
-  for (int c = 0; c < C::NC; ++c) kt[c] = bm[c ^ C::g0()] + kSignBias - bm[c];
 }
 
 // Byte masks of the four decisions of a butterfly: bytes 1 and 3 of t0 and
@@ -468,10 +491,10 @@ __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], c
     for (int ph = 0; ph < S::P; ++ph) {
       const uint32_t wa = pa[ph], wb = pb[ph];
       uint32_t x0, x1;
-      asm("prmt.b32 %0, %1, %2, 0x6420;" : "=r"(x0) : "r"(wa), "r"(wb));
-      asm("prmt.b32 %0, %1, %2, 0x6521;" : "=r"(x1) : "r"(wa), "r"(wb));
-      pkv[ph][0] = __vmaxu2(x0 ^ 0x00800080u, 0x00010001u) - 0x00010001u;
-      pkv[ph][1] = __vmaxu2(x1 ^ 0x00800080u, 0x00010001u) - 0x00010001u;
+      asm("prmt.b32 %0, %1, %2, 0xC480;" : "=r"(x0) : "r"(wa), "r"(wb));
+      asm("prmt.b32 %0, %1, %2, 0xD591;" : "=r"(x1) : "r"(wa), "r"(wb));
+      pkv[ph][0] = soft_lanes(x0);
+      pkv[ph][1] = soft_lanes(x1);
       pkv[ph][2] = 0u;
     }
     gA.rel += 2 * S::P;
