@@ -155,7 +155,9 @@ int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p) {
   p->entry = find_entry(c->K, c->R, c->gens, T, c->P != 0);
   if (p->entry < 0) return PBVD_EUNSUPPORTED;
   const KernelEntry& e = reg.entries[p->entry];
-  const int64_t jmax = (int64_t)c->D + c->L;
+  // survivor records per pair: D + L, rounded up to whole blocks of 8 (the
+  // latency kernel stores records eight stages at a time)
+  const int64_t jmax = ((int64_t)c->D + c->L + 7) & ~7LL;
   p->rec_words = (int)(((jmax * e.words_per_stage) + 3) & ~3LL);
   int smem = c->cfg.survivors_in_smem;
   if (smem < 0) {
@@ -685,7 +687,7 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
   bps += bps & 1;  // whole pairs per segment
   S = (int)ceil_div(nb, bps);
   const KernelEntry& e = registry().entries[p.entry];
-  const int64_t jmax = (int64_t)c->D + c->L;
+  const int64_t jmax = ((int64_t)c->D + c->L + 7) & ~7LL;
   const size_t slice_words = (size_t)jmax * (size_t)(bps / 2) * e.words_per_stage;
   size_t llr_bytes = 0;
   pbvd_llr_count(c, n_stages, &llr_bytes);

@@ -7,12 +7,15 @@
 // path metrics of states 2j and 2j+1 (natural order, PB A in the low and PB
 // B in the high 16 bits) enter, the successors j and j + 32 leave (Sec.
 // III-B butterfly, Eq. (1)), and the next stage's inputs are fetched from
-// lanes 2j mod 32 and 2j+1 mod 32 with four shuffles.  The four decisions of
-// a stage are packed by ballots into a four-word record in natural state
-// order: word 2x + (u >> 5), bit u & 31, set when state u of PB x kept its
-// upper branch (the one from S_2j).  The traceback then needs no layout
-// arithmetic: the predecessor of u is 2 (u mod 32) + (1 - bit) and the
-// decoded bit is u >> 5 (Algorithm 1).  Sixteen lanes walk each PB in
+// lanes 2j mod 32 and 2j+1 mod 32 with four shuffles.  Lane j keeps the four
+// decisions of its butterfly for eight consecutive records in one word (byte
+// 2h + x for successor j + 32h of PB x, bit = record mod 8; a set bit means
+// the upper branch, the one from S_2j, was kept) and stores it once per
+// eight records: block m of a pair's records is 32 words, word j from lane
+// j.  The traceback needs no layout arithmetic: the survivor bit of state u
+// at record r is bit 8 (2 (u >> 5) + x) + (r & 7) of word u & 31 of block
+// r >> 3, the predecessor is 2 (u mod 32) + (1 - bit) and the decoded bit is
+// u >> 5 (Algorithm 1).  Sixteen lanes walk each PB in
 // speculative byte-aligned segments (each checked against the exact exit
 // state of the segment above and re-walked on a mismatch, so the result is
 // exact).
@@ -68,9 +71,10 @@ __device__ __forceinline__ void warp_stage_soft(const KArgs& a, const PbRun& g, 
 // bm_al: metric of the lane's codeword alpha(2j); bm_co = 254 R - bm_al is
 // that of its complement, the codeword of the other three branches' pairs
 // (beta = gamma = ~alpha, theta = alpha when every generator taps both ends).
-// Returns the record words of the stage (upper-kept bits of states 0..63).
+// Returns the lane's four decisions as 0x00 / 0xFF bytes (byte 2h + x: state
+// j + 32h of PB x kept its upper branch).
 template <class C>
-__device__ __forceinline__ uint4 warp_acs(uint32_t& X, uint32_t& Y, uint32_t bm_al, int lane) {
+__device__ __forceinline__ uint32_t warp_acs(uint32_t& X, uint32_t& Y, uint32_t bm_al, int lane) {
   constexpr uint32_t SUM = (uint32_t)(254 * C::R) * 0x00010001u;
   const uint32_t bm_co = SUM - bm_al;
   const uint32_t c1 = Y + bm_co, c3 = Y + bm_al;
@@ -85,14 +89,9 @@ __device__ __forceinline__ uint4 warp_acs(uint32_t& X, uint32_t& Y, uint32_t bm_
   // t = 0x8000 + (lower candidate - upper candidate) per lane
   const uint32_t t0 = c1 + kSignBias - X - bm_al;
   const uint32_t t1 = c3 + kSignBias - X - bm_co;
-  uint4 rec;
-  rec.x = __ballot_sync(0xffffffffu, (t0 & 0x00008000u) != 0u);
-  rec.y = __ballot_sync(0xffffffffu, (t1 & 0x00008000u) != 0u);
-  rec.z = __ballot_sync(0xffffffffu, (t0 & 0x80000000u) != 0u);
-  rec.w = __ballot_sync(0xffffffffu, (t1 & 0x80000000u) != 0u);
   X = lane < 16 ? a0 : a1;
   Y = lane < 16 ? b0 : b1;
-  return rec;
+  return decision_bytes(t0, t1);
 }
 
 // Known-start or zero metrics for one PB's half of the lane's two states.
@@ -133,8 +132,13 @@ __device__ __forceinline__ void warp_decode_pair(const KArgs& a, const PairWork&
   uint32_t X = 0u, Y = 0u;
   if (gA.delta == 0) warp_reinit(X, Y, lane, 0x0000ffffu, gA.known_start);
   if (gB.delta == 0 && wk.hasB) warp_reinit(X, Y, lane, 0xffff0000u, gB.known_start);
-  const int64_t rec_stride = a.surv_pairs * (int64_t)a.surv_rs;
-  uint32_t* gsv = a.surv + gslot * a.surv_rs;
+  // block m of the pair's records: svs + 32 m (shared) or gsv + 32 m
+  // surv_pairs (global, pair slots interleaved block by block)
+  const int64_t blk_stride = 32 * a.surv_pairs;
+  uint32_t* gsv = a.surv + gslot * 32;
+  uint32_t dacc = 0u;
+  const int cs = (8 - (L & 7)) & 7;   // (i0 - L) & 7 for i0 a multiple of 8
+  const int us = (L + 7) & 7;         // u with (i0 + u - L) & 7 == 7
   constexpr int RENORM_BLOCKS = Shape<C, 1>::RENORM_STAGES / U;
   static_assert(RENORM_BLOCKS >= 1, "renormalisation interval shorter than a block");
   constexpr uint32_t RENORM_BASE = Shape<C, 1>::RENORM_BASE;
@@ -184,23 +188,40 @@ __device__ __forceinline__ void warp_decode_pair(const KArgs& a, const PairWork&
     const uint32_t* trow = tab + (i0 % CH) * C::NC + al;
 #pragma unroll
     for (int u = 0; u < U; ++u) bmv[u] = trow[u * C::NC];
-    // blocks holding a PB's first stage (re-initialisation) or the end run checked
-    const bool plain = i0 + U <= I && (gA.delta == 0 || gA.delta < i0 || gA.delta >= i0 + U) &&
-                       (!wk.hasB || gB.delta == 0 || gB.delta < i0 || gB.delta >= i0 + U);
+    // blocks wholly inside [L, I - 1) that hold no PB's first stage run without
+    // per-stage checks: record r = i - L has r & 7 = (cs + u) & 7, and the
+    // word of a block of eight records is complete at u == us
+    // (the last block always runs checked: it stores the final, partial word)
+    const bool plain = i0 >= L && i0 + U < I && (gA.delta < i0 || gA.delta >= i0 + U) &&
+                       (!wk.hasB || gB.delta < i0 || gB.delta >= i0 + U);
+    if (plain) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u;
-      if (!plain) {
+      for (int u = 0; u < U; ++u) {
+        const uint32_t d = warp_acs<C>(X, Y, bmv[u], lane);
+        const uint32_t col = 0x01010101u << ((cs + u) & 7);
+        dacc = (dacc & ~col) | (d & col);
+        if (u == us) {
+          const int m = (i0 + u - L) >> 3;
+          if constexpr (SMEM) svs[(int64_t)m * 32 + lane] = dacc;
+          else gsv[(int64_t)m * blk_stride + lane] = dacc;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u;
         if (i >= I) break;
         if (i == gA.delta && i != 0) warp_reinit(X, Y, lane, 0x0000ffffu, gA.known_start);
         if (i == gB.delta && i != 0) warp_reinit(X, Y, lane, 0xffff0000u, gB.known_start);
-      }
-      const uint4 rec = warp_acs<C>(X, Y, bmv[u], lane);
-      if (i >= L && lane == 0) {
-        if constexpr (SMEM) {
-          *reinterpret_cast<uint4*>(svs + (int64_t)(i - L) * 4) = rec;
-        } else {
-          *reinterpret_cast<uint4*>(gsv + (int64_t)(i - L) * rec_stride) = rec;
+        const uint32_t d = warp_acs<C>(X, Y, bmv[u], lane);
+        if (i >= L) {
+          const int r = i - L;
+          const uint32_t col = 0x01010101u << (r & 7);
+          dacc = (dacc & ~col) | (d & col);
+          if ((r & 7) == 7 || i == I - 1) {
+            if constexpr (SMEM) svs[(int64_t)(r >> 3) * 32 + lane] = dacc;
+            else gsv[(int64_t)(r >> 3) * blk_stride + lane] = dacc;
+          }
         }
       }
     }
@@ -226,17 +247,13 @@ __device__ __forceinline__ void warp_decode_pair(const KArgs& a, const PairWork&
   const bool active = jtop >= 0 && lo <= jtop;
   const int hs = (q == top) ? jtop : min(jtop, hi + kWarpLambda);
   const int emit_top = min(hi, gp.nout - 1);
-  auto record = [&](int j) -> uint2 {
-    const uint32_t* r = SMEM ? svs + (int64_t)j * 4 : gsv + (int64_t)j * rec_stride;
-    return xb ? *reinterpret_cast<const uint2*>(r + 2) : *reinterpret_cast<const uint2*>(r);
-  };
   auto walk = [&](int from, int to, uint32_t u, int g_at, uint32_t& g) -> uint32_t {
     uint32_t acc = 0u;
     for (int j = from; j >= to; --j) {
-      const uint2 w = record(j);
+      const uint32_t* blk = SMEM ? svs + (int64_t)(j >> 3) * 32 : gsv + (int64_t)(j >> 3) * blk_stride;
+      const uint32_t word = blk[u & 31u];
       if (j == g_at) g = u;
-      const uint32_t word = (u & 32u) ? w.y : w.x;
-      const uint32_t upper = (word >> (u & 31u)) & 1u;
+      const uint32_t upper = (word >> (((u >> 5) * 2 + xb) * 8 + (j & 7))) & 1u;
       acc = (acc << 1) | (u >> 5);
       u = ((u << 1) & 62u) | (upper ^ 1u);
       if ((j & 7) == 0 && j <= emit_top) {
