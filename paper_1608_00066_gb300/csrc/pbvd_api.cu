@@ -1035,8 +1035,9 @@ int pbvd_stream_open(pbvd_stream** out, pbvd_ctx* c, size_t max_push, uint8_t* d
   s->P = e.P;
   s->R = c->R;
   s->max_push = max_push;
-  // records of the oldest unreleased stage up to the last stage of a push
-  s->H = (int)(max_push + c->D + c->L + 2 * e.P);
+  // records of the oldest unreleased stage up to the last stage of a push,
+  // rounded up to whole blocks of eight stages with one block to spare
+  s->H = (int)((max_push + c->D + c->L + 2 * e.P + 8 + 7) & ~(size_t)7);
   s->d_out = d_out;
   s->out_cap = out_capacity;
   // known start: S_0 at 0, every other state at 8192 (lane A)

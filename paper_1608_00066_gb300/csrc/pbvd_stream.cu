@@ -20,6 +20,7 @@
 // load per stage.  The stages of a partial period left at the end of a push
 // are copied to the stream's carry buffer and decoded first by the next push.
 #include "pbvd_device.cuh"
+#include "pbvd_warp.cuh"
 
 namespace pbvd {
 
@@ -289,8 +290,226 @@ StreamKernelEntry make_stream_entry() {
   return e;
 }
 
+
+// ------------------------------------------------ one warp per K=7 stream --
+//
+// The 64-state streams run on the latency core of pbvd_warp.cuh: one warp
+// per stream (lane A of the packed metrics; lane B unused), lane j owning
+// butterfly j in natural state order, so every push decodes all its stages
+// (a period of one stage: no carry).  Records go to the stream's ring in
+// blocks of eight stages: stage t's decisions are in block (t >> 3) mod
+// (H / 8), word u & 31 for state u, bit 16 (u >> 5) + (t & 7); lane j keeps
+// the block's word in a register and stores it when the block is complete or
+// the push ends (the next push reloads a partly filled word).  Each release
+// walk prefetches whole blocks of 128 bytes into its lane's part of shared
+// memory with cp.async.
+
+constexpr int kStreamWarpSC = 64;      // stages per staged chunk
+constexpr int kStreamWarpNB = 4;       // ring blocks in flight per walking lane
+
+template <class C>
+struct StreamWarpSmem {
+  static constexpr int CB = ((kStreamWarpSC * C::R + 15) / 16 + 1) * 16;
+  static constexpr int RAW_WORDS = 2 * CB / 4;
+  static constexpr int TAB_WORDS = kStreamWarpSC * C::NC;
+  static constexpr int WALK_WORDS = 32 * kStreamWarpNB * 32;
+  static constexpr int WORDS = RAW_WORDS + TAB_WORDS + WALK_WORDS;
+};
+
+template <class C>
+__device__ __forceinline__ void stream_warp_walk(const StreamDev& sd, int64_t start, int64_t lo, int64_t hi_out,
+                                                 uint32_t* wring) {
+  const int HB = sd.H >> 3;
+  const int64_t b_top = start >> 3, b_lo = lo >> 3;
+  const int nblk = (int)(b_top - b_lo + 1);
+  int issued = 0;
+  auto issue = [&]() {
+    if (issued < nblk) {
+      const int64_t b = b_top - issued;
+      const uint32_t* src = sd.ring + (int64_t)(b % HB) * 32;
+      const unsigned d = (unsigned)__cvta_generic_to_shared(wring + (issued % kStreamWarpNB) * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * q), "l"(src + 4 * q));
+    }
+    ++issued;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+#pragma unroll
+  for (int q = 0; q < kStreamWarpNB - 1; ++q) issue();
+  uint32_t u = 0u, acc = 0u;
+  int64_t t = start;
+  for (int k = 0; k < nblk; ++k) {
+    issue();
+    asm volatile("cp.async.wait_group %0;" ::"n"(kStreamWarpNB - 1) : "memory");
+    const uint32_t* blk = wring + (k % kStreamWarpNB) * 32;
+    const int64_t tb = (b_top - k) << 3;   // first stage of the block
+    for (; t >= tb && t >= lo; --t) {
+      const uint32_t word = blk[u & 31u];
+      const uint32_t upper = (word >> (16u * (u >> 5) + (uint32_t)(t & 7))) & 1u;
+      acc = (acc << 1) | (u >> 5);
+      u = ((u << 1) & 62u) | (upper ^ 1u);
+      if ((t & 7) == 0 && t < hi_out) {
+        const int64_t rem = hi_out - t;
+        const uint32_t keep = rem >= 8 ? 0xffu : ((1u << rem) - 1u);
+        sd.out[t >> 3] = (uint8_t)(acc & keep);
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <class C>
+__global__ void __launch_bounds__(32) pbvd_stream_warp_kernel(const __grid_constant__ StreamLaunch p) {
+  static_assert(C::v == 6, "one butterfly per lane: 64 states");
+  using SW = StreamWarpSmem<C>;
+  constexpr int R = C::R, SC = kStreamWarpSC, CB = SW::CB;
+  __shared__ __align__(16) uint32_t smem[SW::WORDS];
+  const int idx = blockIdx.x;
+  if (idx >= p.count) return;
+  const StreamDev& sd = p.d[idx];
+  const int lane = threadIdx.x & 31;
+  int8_t* raw = reinterpret_cast<int8_t*>(smem);
+  uint32_t* tab = smem + SW::RAW_WORDS;
+  uint32_t* wring = smem + SW::RAW_WORDS + SW::TAB_WORDS + lane * (kStreamWarpNB * 32);
+
+  const int nproc = sd.nnew;   // one-stage periods: every stage is decoded now
+  const int64_t t0 = sd.t0;
+  const int HB = sd.H >> 3;
+  const uint32_t al = C::alpha((uint32_t)(2 * lane));
+  uint32_t X = sd.pm[2 * lane], Y = sd.pm[2 * lane + 1];
+  // the word of the block holding stage t0, partly filled by the last push
+  uint32_t dacc = (t0 & 7) ? sd.ring[(int64_t)((t0 >> 3) % HB) * 32 + lane] : 0u;
+
+  const int nchunk = (nproc + SC - 1) / SC;
+  int64_t cb0 = stage_stream_chunk<R>(sd.llr, sd.nnew, 0, SC, raw, lane, 32);
+  int64_t cb1 = 0;
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  constexpr int RENORM = Shape<C, 1>::RENORM_STAGES;
+  constexpr uint32_t RENORM_BASE = Shape<C, 1>::RENORM_BASE;
+  int since_renorm = 0;
+  for (int c = 0; c < nchunk; ++c) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    {
+      const int8_t* buf = raw + (c & 1) * CB;
+      const int64_t cbase = (c & 1) ? cb1 : cb0;
+#pragma unroll
+      for (int h = 0; h < SC / 32; ++h) {
+        const int sl = lane + 32 * h;
+        const int i = c * SC + sl;
+        uint32_t pk[3] = {0u, 0u, 0u};
+        if (i < nproc) {
+          const uint8_t* src = reinterpret_cast<const uint8_t*>(buf) + ((int64_t)i * R - cbase);
+#pragma unroll
+          for (int q = 0; q < R; ++q) pk[q] = pack_soft(src[q], 0u);
+        }
+#pragma unroll
+        for (int cw = 0; cw < C::NC; ++cw) {
+          uint32_t m = 0u;
+#pragma unroll
+          for (int q = 0; q < R; ++q) m += ((cw >> (R - 1 - q)) & 1) ? pk[q] : kLamMax2 - pk[q];
+          tab[sl * C::NC + cw] = m;
+        }
+      }
+    }
+    __syncwarp();
+    if (c + 1 < nchunk) {
+      const int64_t k0 = (int64_t)(c + 1) * SC;
+      const int64_t cb = stage_stream_chunk<R>(sd.llr, sd.nnew, k0, k0 + SC, raw + ((c + 1) & 1) * CB, lane, 32);
+      if ((c + 1) & 1) cb1 = cb; else cb0 = cb;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int iend = min(nproc, (c + 1) * SC);
+    const int ic = c * SC;                               // first stage of the chunk
+    const uint32_t* trow = tab + al;                     // trow[(i - ic) * NC]: stage i's metric
+    auto renorm = [&]() {
+      since_renorm = 0;
+      const uint32_t ref = __shfl_sync(0xffffffffu, X, 0);  // state 0
+      X = X + RENORM_BASE - ref;
+      Y = Y + RENORM_BASE - ref;
+    };
+    auto step = [&](int i) {
+      const uint32_t d = warp_acs<C>(X, Y, trow[(i - ic) * C::NC], lane);
+      const int64_t t = t0 + i;
+      const uint32_t col = 0x01010101u << (uint32_t)(t & 7);
+      dacc = (dacc & ~col) | (d & col);
+      if ((t & 7) == 7 || i == nproc - 1) sd.ring[(int64_t)((t >> 3) % HB) * 32 + lane] = dacc;
+      if (++since_renorm == RENORM) renorm();
+    };
+    int i = c * SC;
+    for (; i < iend && ((t0 + i) & 7) != 0; ++i) step(i);
+    // whole blocks of eight stages (t = 8m .. 8m + 7) before the push's last
+    // stage: no per-stage checks, the word stored once per block
+    for (; i + 8 <= iend && i + 8 < nproc; i += 8) {
+      if (since_renorm + 8 > RENORM) renorm();
+      uint32_t bmv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) bmv[u] = trow[(i - ic + u) * C::NC];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t d = warp_acs<C>(X, Y, bmv[u], lane);
+        const uint32_t col = 0x01010101u << u;
+        dacc = (dacc & ~col) | (d & col);
+      }
+      sd.ring[(int64_t)(((t0 + i) >> 3) % HB) * 32 + lane] = dacc;
+      since_renorm += 8;
+    }
+    for (; i < iend; ++i) step(i);
+  }
+  if (nproc > 0) {
+    const uint32_t ref = __shfl_sync(0xffffffffu, X, 0);
+    X = X + RENORM_BASE - ref;
+    Y = Y + RENORM_BASE - ref;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!sd.final_) {
+    sd.pm[2 * lane] = X;
+    sd.pm[2 * lane + 1] = Y;
+  }
+  __threadfence_block();
+  __syncwarp();
+
+  // releases: segments whose trigger stage exists, or everything at close;
+  // one walk per lane at a time
+  const int64_t tend = t0 + nproc;
+  const int64_t D = sd.D, L = sd.L;
+  const int64_t first = sd.released;
+  int64_t nseg = 0;
+  if (tend >= first + D + L) nseg = (tend - L - first) / D;
+  const bool last = sd.final_ != 0;
+  const int64_t nwalk = nseg + ((last && first + nseg * D < tend) ? 1 : 0);
+  for (int64_t w = lane; w < nwalk; w += 32) {
+    const int64_t lo = first + w * D;
+    const bool is_tail = (w == nseg);
+    const int64_t hi_out = is_tail ? tend : lo + D;
+    const int64_t start = is_tail ? tend - 1 : lo + D + L - 1;
+    stream_warp_walk<C>(sd, start, lo, hi_out, wring);
+  }
+}
+
+template <class C>
+cudaError_t launch_stream_warp(const StreamLaunch& p, cudaStream_t s) {
+  if (p.count <= 0 || p.count > kStreamsPerLaunch) return cudaErrorInvalidValue;
+  pbvd_stream_warp_kernel<C><<<p.count, 32, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <class C>
+StreamKernelEntry make_stream_warp_entry() {
+  StreamKernelEntry e;
+  e.K = C::K;
+  e.R = C::R;
+  for (int r = 0; r < 3; ++r) e.gens[r] = C::gen(r);
+  e.T = 32;
+  e.P = 1;
+  e.words_per_stage = 4;
+  e.launch = &launch_stream_warp<C>;
+  return e;
+}
+
 int register_stream(StreamKernelEntry* out, int cap) {
-  const StreamKernelEntry all[] = {make_stream_entry<K7, 8>(), make_stream_entry<K9, 8>()};
+  const StreamKernelEntry all[] = {make_stream_warp_entry<K7>(), make_stream_entry<K9, 8>()};
   int n = 0;
   for (const StreamKernelEntry& e : all)
     if (n < cap) out[n++] = e;
