@@ -1151,11 +1151,21 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   traceback_pair<C, T, SMEM>(a, gA, gB, wk.hasB, J, gslot, scratch, svs);
 }
 
+// Minimum resident CTAs of 256 threads the compiler is asked to allow: 2 (at
+// most 128 registers) for the 256-state code at eight threads per pair,
+// whose 2049-warp launch for a 2^24-bit stream then fits one wave (16 warps
+// per SM) and runs 10% faster without spilling; 1 elsewhere (the other
+// instances either use fewer registers anyway or slow down when squeezed).
+template <class C, int T>
+__host__ __device__ constexpr int decode_min_ctas() {
+  return (C::N == 256 && T == 8) ? 2 : 1;
+}
+
 // Plain launch: pair p of blocks [b_first, n_blocks) of one stream.  SMEM:
 // survivor records of each group in shared memory (a.smem_rec_words words
 // per group), else in a.surv.
 template <class C, int T, bool PUNCT, bool SMEM>
-__global__ void __launch_bounds__(256, 1) pbvd_decode_kernel(const KArgs a) {
+__global__ void __launch_bounds__(256, decode_min_ctas<C, T>()) pbvd_decode_kernel(const KArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int groups_per_cta = blockDim.x / T;
   const int gl = threadIdx.x / T;
