@@ -6,12 +6,14 @@ pointed at a known launch (skip the warm-up launches, capture the next).
     python -m paper_1608_00066_gb300.prof k9     [--tune JSON] ...
     python -m paper_1608_00066_gb300.prof batch  ...
     python -m paper_1608_00066_gb300.prof stream ...
+    python -m paper_1608_00066_gb300.prof frame  [--tune JSON] ...
 
 Workloads (the benchmark's):
   k7     K=7 r1/2 (171,133) terminated stream, 2^24 info bits, 3 dB, D=512 L=42
   k9     K=9 r1/3 (557,663,711) terminated stream, 2^24 info bits, 2 dB, D=1024 L=64
   batch  10,000 mixed-code frames (K7 r1/2, K7 r3/4, K9 r1/3), one persistent launch
   stream 64 continuous K7 r1/2 streams, 4096 stages per push, one launch per push
+  frame  one K7 r1/2 frame of 4096 info bits, 3 dB, D=512 L=42 (latency case)
 
 Prints one line per launch set: the workload, the configuration and the mean
 device time per launch (CUDA events; L2 not flushed, so do not use it as a
@@ -95,7 +97,7 @@ def run_streams(torch, warmup, reps, n_streams=64, chunk=4096):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("target", choices=["k7", "k9", "batch", "stream"])
+    ap.add_argument("target", choices=["k7", "k9", "batch", "stream", "frame"])
     ap.add_argument("--tune", default="", help="JSON kernel configuration for k7 / k9")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reps", type=int, default=3)
@@ -107,6 +109,8 @@ def main(argv=None):
         ms, cfg = run_stream_decode(torch, synth.K7_R12, 1 << 24, 3.0, 2003, 512, 42, tune, args.warmup, args.reps)
     elif args.target == "k9":
         ms, cfg = run_stream_decode(torch, synth.K9_R13, 1 << 24, 2.0, 3001, 1024, 64, tune, args.warmup, args.reps)
+    elif args.target == "frame":
+        ms, cfg = run_stream_decode(torch, synth.K7_R12, 4096, 3.0, 1001, 512, 42, tune, args.warmup, args.reps)
     elif args.target == "batch":
         ms, cfg = run_batch(torch, args.warmup, args.reps)
     else:
