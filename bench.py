@@ -6,9 +6,9 @@ and packed output, for a terminated stream of 2^24 information bits of the
 K=7 rate-1/2 (171,133) code at Eb/N0 = 3 dB, decoded in blocks of D=512
 stages with L=42 overlap stages (the code, D and L of the paper's
 experiments).  value = decoded information bits / device time, inputs
-resident in HBM; e2e = the same through host buffers (pinned host -> device
-copy, decode, device -> host copy of the decoded bits inside the timed
-region).
+resident in HBM; e2e = the same through page-locked host buffers (host ->
+device copies of the soft values, decode, device -> host copy of the decoded
+bits, all inside the timed region).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -287,26 +287,37 @@ def run_ours(args, rank: int, world: int):
     bits = np.unpackbits(d_out.cpu().numpy(), bitorder="little")[:K_INFO]
     ber = float((bits != frame.msg).mean())
 
-    # end to end through host buffers: pbvd_decode_host copies each run of
-    # blocks host -> device, decodes it and copies its bits back, with the
-    # copies of later runs overlapping the decoding of earlier ones
+    # end to end through page-locked host buffers: pbvd_decode_host copies
+    # runs of blocks host -> device, decodes each run as soon as its copy has
+    # arrived and copies its bits back, later copies overlapping earlier
+    # decodes; beside it, its direct-access mode (the kernel reads and writes
+    # the host buffers in place).  Each step is timed on its own with L2
+    # flushed before it, so no step finds the input in L2.
     h_llr = torch.from_numpy(frame.llr).pin_memory()
     h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
-    for _ in range(max(1, args.warmup)):
-        dec.decode_host(h_llr, n, out=h_out, stream=stream)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        dec.decode_host(h_llr, n, out=h_out, stream=stream)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    host_bits = np.unpackbits(h_out.numpy(), bitorder="little")[:K_INFO]
-    if not np.array_equal(host_bits, bits):
-        raise RuntimeError("host-memory decode differs from the device decode")
 
-    ms, e2e_ms = max_over_ranks([ms, e2e_ms], world)
+    def time_host(segments):
+        for _ in range(max(1, args.warmup)):
+            dec.decode_host(h_llr, n, out=h_out, segments=segments, stream=stream)
+        barrier()
+        t0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        t1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for s in range(args.steps):
+            flush.zero_()
+            t0[s].record(stream)
+            dec.decode_host(h_llr, n, out=h_out, segments=segments, stream=stream)
+            t1[s].record(stream)
+        barrier()
+        host_bits = np.unpackbits(h_out.numpy(), bitorder="little")[:K_INFO]
+        if not np.array_equal(host_bits, bits):
+            raise RuntimeError("host-memory decode (segments=%d) differs from the device decode" % segments)
+        h_out.zero_()
+        return sum(t0[s].elapsed_time(t1[s]) for s in range(args.steps)) / args.steps
+
+    e2e_ms = time_host(0)
+    e2e_direct_ms = time_host(-1)
+
+    ms, e2e_ms, e2e_direct_ms = max_over_ranks([ms, e2e_ms, e2e_direct_ms], world)
 
     batched = run_batched(args) if (rank == 0 and not args.no_batch) else None
     latency = run_latency(args) if (rank == 0 and not args.no_batch) else None
@@ -338,8 +349,13 @@ def run_ours(args, rank: int, world: int):
                          "peak": hbm_peak, "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                          "algorithmic_bytes": alg_bytes, "peak_source": hbm_src},
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(frame.llr.nbytes),
-                "d2h_bytes_per_step": int(nbytes), "api": "pbvd_decode_host (pinned host buffers, copies "
-                "overlapped with decoding)"},
+                "d2h_bytes_per_step": int(nbytes),
+                "api": "pbvd_decode_host (page-locked host buffers; copies of runs of blocks overlapped "
+                       "with their decoding)",
+                "direct_access": {"value": round(aggregate_gbps(K_INFO, world, e2e_direct_ms), 3), "unit": UNIT,
+                                  "api": "pbvd_decode_host segments=-1: the kernel reads and writes the "
+                                  "page-locked host buffers in place"},
+                "l2": "flushed before each step"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "ber": ber,

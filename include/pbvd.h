@@ -101,29 +101,42 @@ PBVD_API void pbvd_destroy(pbvd_ctx *ctx);
 PBVD_API int pbvd_decode(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
                 uint8_t *d_out, void *stream);
 
-/* Decodes a stream held in HOST memory, overlapping the host-device copies
- * with the decoding, after the multi-stream pipeline of Sec. IV-C (Eq. (7)):
- * the stream's blocks are cut into `segments` runs of whole pairs of blocks
- * (0 = automatic: up to 8 runs of at least 1024 blocks; at most 64); the soft
- * values of each run go host -> device in order on one copy stream, each run
- * is decoded on one of sixteen compute streams as soon as its own values and
- * those of the next run (its last block reads L stages beyond the run) have
- * arrived, and its packed bits go device -> host on the same compute stream.
- * Runs decode concurrently, so the GPU fills up while later runs are still
- * being copied.
- *   h_llr      host soft values, laid out as d_llr of pbvd_decode; page-locked
- *              memory is needed for the copies to overlap (pageable memory
- *              works but is copied synchronously by the driver)
+/* Decodes a stream held in HOST memory, in one of two ways.
+ * Copy pipeline (segments >= 0), after the multi-stream scheme of Sec. IV-C
+ * (Eq. (7)): the stream's blocks are cut into runs of whole pairs of blocks;
+ * the soft values go host -> device in order on one copy stream, copy i
+ * ending L stages into run i + 1 (the last stage that run i's blocks read),
+ * each run is decoded on one of sixteen compute streams as soon as its copy
+ * has arrived, and its packed bits go device -> host on the same compute
+ * stream.  Runs decode concurrently, so the GPU fills up while later runs
+ * are still being copied.
+ * Direct access (segments = -1): both host buffers must be page-locked and
+ * mapped into the device's address space (cudaHostAlloc / cudaMallocHost /
+ * cudaHostRegister with unified addressing, as cudaPointerGetAttributes
+ * reports); the decode kernel of pbvd_decode then reads the soft values
+ * from host memory and writes the packed bits to host memory itself, over
+ * the host-device link, with no staging copy and no device copy of the
+ * stream (the halo stages of Sec. III-A cross the link twice).  Slower than
+ * the copy pipeline on a GB300: the kernel's many small reads use the link
+ * poorly.
+ *   h_llr      host soft values, laid out as d_llr of pbvd_decode
  *   h_out      host, ceil(n_stages / 8) bytes, written as d_out of pbvd_decode
+ *   segments   0 = copy pipeline with an automatic number of runs (up to 6
+ *              runs of at least 1024 blocks); > 0 = copy pipeline with that
+ *              many runs (at most 64); -1 = direct access (PBVD_EINVAL,
+ *              nothing enqueued, when a buffer is not mapped page-locked
+ *              memory).  Pageable memory works in the copy pipeline but is
+ *              copied synchronously by the driver.
  *   stream     the caller's stream: the work starts after what is already
  *              queued on it, and work queued on it later waits for the whole
  *              decode, so h_out is complete once the stream reaches that point
- * The bits are exactly those of pbvd_decode with the same context.  Uses the
- * context's configuration with survivors in global memory; the context owns
- * the device copies of the stream, its copy and compute streams and events,
- * grown on first use of a larger size (device allocations that synchronise).
- * Host buffers must stay valid until the stream has passed the call; calls
- * on one context must not overlap on the GPU. */
+ * The bits are exactly those of pbvd_decode with the same context.  The copy
+ * pipeline uses the context's configuration with survivors in global
+ * memory; the context owns the device copies of the stream, its copy and
+ * compute streams and events, grown on first use of a larger size (device
+ * allocations that synchronise).  Host buffers must stay valid until the
+ * stream has passed the call; calls on one context must not overlap on the
+ * GPU. */
 PBVD_API int pbvd_decode_host(pbvd_ctx *ctx, const int8_t *h_llr, size_t n_stages,
                               uint8_t *h_out, int segments, void *stream);
 

@@ -250,6 +250,19 @@ int host_pipeline_setup(pbvd_ctx* c) {
   return PBVD_OK;
 }
 
+// The device address of host memory the kernels may read and write in
+// place: page-locked memory mapped into the device's address space
+// (cudaHostAlloc / cudaMallocHost / cudaHostRegister under unified
+// addressing).  Null for pageable or unknown memory.
+void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 template <class T>
 int grow_device(T** p, size_t* cap, size_t bytes) {
   if (bytes <= *cap && *p) return PBVD_OK;
@@ -285,6 +298,10 @@ struct pbvd_batch {
   int32_t* d_counter;
   uint32_t* d_surv;
   size_t surv_bytes;
+  void* h_stage;        // page-locked staging of the work list (pairs, tiles)
+  size_t h_stage_cap;   // bytes
+  cudaEvent_t staged;   // the last upload from h_stage
+  int staged_pending;
 };
 
 namespace {
@@ -363,42 +380,54 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
   PBVD_CUDA(cudaGetDevice(&dev));
   if (dev != c0->device) return PBVD_EINVAL;
 
-  // blocks per slot, longest forward range first, paired neighbours
-  std::vector<HostPb> pbs[kBatchSlots];
+  // blocks per slot, longest forward range first (a counting sort on the
+  // forward length, stable in item and block order), paired neighbours
+  std::vector<const int8_t*> item_end(n_items);
   for (size_t i = 0; i < n_items; ++i) {
-    const pbvd_ctx* c = items[i].ctx;
-    const int64_t n = (int64_t)items[i].n_stages;
-    const int64_t nb = ceil_div(n, c->D);
-    for (int64_t b = 0; b < nb; ++b) pbs[item_slot[i]].push_back({(int)i, b, block_len(n, c->D, c->L, b)});
+    size_t cnt = 0;
+    pbvd_llr_count(items[i].ctx, items[i].n_stages, &cnt);
+    item_end[i] = items[i].d_llr + cnt;
+  }
+  std::vector<HostPb> pbs[kBatchSlots];
+  std::vector<int64_t> start;
+  for (int s = 0; s < kBatchSlots; ++s) {
+    if (!slot_ctx[s]) continue;
+    const int D = slot_ctx[s]->D, L = slot_ctx[s]->L;
+    start.assign((size_t)D + 2 * L + 2, 0);
+    int64_t total = 0;
+    for (size_t i = 0; i < n_items; ++i) {
+      if (item_slot[i] != s) continue;
+      const int64_t n = (int64_t)items[i].n_stages, nb = ceil_div(n, D);
+      for (int64_t b = 0; b < nb; ++b) ++start[block_len(n, D, L, b)];
+      total += nb;
+    }
+    int64_t acc = 0;
+    for (int64_t len = (int64_t)start.size() - 1; len >= 0; --len) {
+      const int64_t c = start[len];
+      start[len] = acc;
+      acc += c;
+    }
+    pbs[s].resize((size_t)total);
+    for (size_t i = 0; i < n_items; ++i) {
+      if (item_slot[i] != s) continue;
+      const int64_t n = (int64_t)items[i].n_stages, nb = ceil_div(n, D);
+      for (int64_t b = 0; b < nb; ++b) {
+        const int len = block_len(n, D, L, b);
+        pbs[s][(size_t)start[len]++] = {(int)i, b, len};
+      }
+    }
   }
   const int cta = 64;
-  std::vector<BatchPair> pairs;
+  size_t n_pairs_all = 0;
+  for (int s = 0; s < kBatchSlots; ++s) n_pairs_all += (pbs[s].size() + 1) / 2;
   std::vector<BatchTile> tiles;
-  std::vector<int> tile_cost;
+  std::vector<int64_t> tile_cost;
   for (int s = 0; s < kBatchSlots; ++s) {
-    std::vector<HostPb>& v = pbs[s];
-    if (v.empty()) continue;
-    std::stable_sort(v.begin(), v.end(), [](const HostPb& x, const HostPb& y) { return x.len > y.len; });
+    const int64_t np = (int64_t)(pbs[s].size() + 1) / 2;
+    if (np == 0) continue;
     const int groups = cta / be.T[s];
-    const int64_t first_pair = (int64_t)pairs.size();
-    for (size_t k = 0; k < v.size(); k += 2) {
-      BatchPair p;
-      std::memset(&p, 0, sizeof(p));
-      for (int h = 0; h < 2; ++h) {
-        const HostPb& q = v[k + (k + h < v.size() ? h : 0)];
-        const pbvd_batch_item& it = items[q.item];
-        size_t cnt = 0;
-        pbvd_llr_count(it.ctx, it.n_stages, &cnt);
-        p.llr[h] = it.d_llr;
-        p.llr_end[h] = it.d_llr + cnt;
-        p.out[h] = it.d_out;
-        p.n[h] = (int64_t)it.n_stages;
-        p.b[h] = q.b;
-      }
-      p.hasB = (k + 1 < v.size()) ? 1 : 0;
-      pairs.push_back(p);
-    }
-    const int64_t np = (int64_t)pairs.size() - first_pair;
+    int64_t first_pair = 0;
+    for (int q = 0; q < s; ++q) first_pair += (int64_t)(pbs[q].size() + 1) / 2;
     for (int64_t t = 0; t < np; t += groups) {
       BatchTile tl;
       tl.slot = s;
@@ -406,15 +435,13 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
       tl.first = first_pair + t;
       tiles.push_back(tl);
       // pairs are sorted, so the tile's first pair is its longest
-      tile_cost.push_back(v[2 * t].len * (1 << (be.K[s] - 1)) * be.T[s] / 2);
+      tile_cost.push_back((int64_t)pbs[s][(size_t)(2 * t)].len * (1 << (be.K[s] - 1)) * be.T[s] / 2);
     }
   }
   // longest tiles first for the dynamic tile queue
   std::vector<size_t> order(tiles.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return tile_cost[x] > tile_cost[y]; });
-  std::vector<BatchTile> sorted(tiles.size());
-  for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
 
   pbvd_batch* b = reuse;
   if (!b) {
@@ -446,7 +473,7 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
   PBVD_CUDA(be.occupancy(&per_sm, cta, smem));
   if (per_sm < 1) return PBVD_EUNSUPPORTED;
   const int grid_cap = per_sm * std::max(1, c0->sm_count - reserve_sms);
-  b->grid = std::max(1, std::min<int>(grid_cap, (int)std::max<size_t>(sorted.size(), 1)));
+  b->grid = std::max(1, std::min<int>(grid_cap, (int)std::max<size_t>(tiles.size(), 1)));
   const int64_t n_slots = (int64_t)b->grid * gmax;
   // one record slot size for every code of the launch, so that the records
   // of different codes in concurrently running CTAs never overlap
@@ -458,18 +485,54 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
       jmax = std::max(jmax, (size_t)(slot_ctx[s]->D + slot_ctx[s]->L));
     }
   const size_t surv = jmax * (size_t)n_slots * rs_max * 4;
-  if ((rc = grow(&b->d_pairs, &b->pairs_cap, pairs.size())) != PBVD_OK) return rc;
-  if ((rc = grow(&b->d_tiles, &b->tiles_cap, sorted.size())) != PBVD_OK) return rc;
+  if ((rc = grow(&b->d_pairs, &b->pairs_cap, n_pairs_all)) != PBVD_OK) return rc;
+  if ((rc = grow(&b->d_tiles, &b->tiles_cap, tiles.size())) != PBVD_OK) return rc;
   if (!b->d_counter) PBVD_CUDA(cudaMalloc(&b->d_counter, sizeof(int32_t)));
   size_t surv_words_cap = b->surv_bytes / 4;
   if ((rc = grow(&b->d_surv, &surv_words_cap, (surv + 3) / 4)) != PBVD_OK) return rc;
   b->surv_bytes = surv_words_cap * 4;
+  // the work list is written into page-locked staging (once the previous
+  // upload from it has left) and uploaded asynchronously
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!pairs.empty())
-    PBVD_CUDA(cudaMemcpyAsync(b->d_pairs, pairs.data(), pairs.size() * sizeof(BatchPair), cudaMemcpyHostToDevice, st));
-  if (!sorted.empty())
-    PBVD_CUDA(cudaMemcpyAsync(b->d_tiles, sorted.data(), sorted.size() * sizeof(BatchTile), cudaMemcpyHostToDevice,
-                              st));
+  const size_t pair_bytes = n_pairs_all * sizeof(BatchPair), tile_bytes = tiles.size() * sizeof(BatchTile);
+  if (b->staged_pending) {
+    PBVD_CUDA(cudaEventSynchronize(b->staged));
+    b->staged_pending = 0;
+  }
+  if (pair_bytes + tile_bytes > b->h_stage_cap) {
+    if (b->h_stage) PBVD_CUDA(cudaFreeHost(b->h_stage));
+    b->h_stage = nullptr;
+    b->h_stage_cap = 0;
+    const size_t cap = (pair_bytes + tile_bytes) + (pair_bytes + tile_bytes) / 2 + 4096;
+    PBVD_CUDA(cudaHostAlloc(&b->h_stage, cap, cudaHostAllocDefault));
+    b->h_stage_cap = cap;
+  }
+  if (!b->staged) PBVD_CUDA(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
+  BatchPair* hp = static_cast<BatchPair*>(b->h_stage);
+  BatchTile* ht = reinterpret_cast<BatchTile*>(static_cast<char*>(b->h_stage) + pair_bytes);
+  size_t k_pair = 0;
+  for (int s = 0; s < kBatchSlots; ++s) {
+    const std::vector<HostPb>& v = pbs[s];
+    for (size_t k = 0; k < v.size(); k += 2) {
+      BatchPair& p = hp[k_pair++];
+      for (int h = 0; h < 2; ++h) {
+        const HostPb& q = v[k + (k + h < v.size() ? h : 0)];
+        const pbvd_batch_item& it = items[q.item];
+        p.llr[h] = it.d_llr;
+        p.llr_end[h] = item_end[q.item];
+        p.out[h] = it.d_out;
+        p.n[h] = (int64_t)it.n_stages;
+        p.b[h] = q.b;
+      }
+      p.hasB = (k + 1 < v.size()) ? 1 : 0;
+      p.pad = 0;
+    }
+  }
+  for (size_t i = 0; i < order.size(); ++i) ht[i] = tiles[order[i]];
+  if (pair_bytes) PBVD_CUDA(cudaMemcpyAsync(b->d_pairs, hp, pair_bytes, cudaMemcpyHostToDevice, st));
+  if (tile_bytes) PBVD_CUDA(cudaMemcpyAsync(b->d_tiles, ht, tile_bytes, cudaMemcpyHostToDevice, st));
+  PBVD_CUDA(cudaEventRecord(b->staged, st));
+  b->staged_pending = 1;
   // kernel arguments
   BatchArgs& a = b->args;
   std::memset(&a, 0, sizeof(a));
@@ -489,7 +552,7 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
   }
   a.pairs = b->d_pairs;
   a.tiles = b->d_tiles;
-  a.ntiles = (int32_t)sorted.size();
+  a.ntiles = (int32_t)tiles.size();
   a.gmax = gmax;
   a.counter = b->d_counter;
   *out = b;
@@ -665,11 +728,19 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
 
 int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t* h_out, int segments,
                      void* stream) {
-  if (!c || !h_llr || !h_out || n_stages == 0 || segments < 0) return PBVD_EINVAL;
+  if (!c || !h_llr || !h_out || n_stages == 0 || segments < -1) return PBVD_EINVAL;
   if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
   int dev = -1;
   PBVD_CUDA(cudaGetDevice(&dev));
   if (dev != c->device) return PBVD_EINVAL;
+  if (segments < 0) {
+    // direct access: the kernel reads the soft values from host memory and
+    // writes the bits back over the host link itself, with no staging copy
+    const int8_t* d_in = static_cast<const int8_t*>(mapped_host(h_llr));
+    uint8_t* d_o = static_cast<uint8_t*>(mapped_host(h_out));
+    if (!d_in || !d_o) return PBVD_EINVAL;
+    return pbvd_decode(c, d_in, n_stages, d_o, stream);
+  }
   // the kernel configuration pbvd_decode would use, survivors in global
   // memory (one workspace slice per compute lane)
   pbvd_ctx cc = *c;
@@ -678,14 +749,23 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
   int rc = plan_decode(&cc, n_stages, &p);
   if (rc != PBVD_OK) return rc;
   const int64_t nb = p.n_blocks;
-  // automatic: up to 8 runs of at least 1024 blocks (more, shorter runs
-  // start their decode sooner but each kernel of a run then underfills the
-  // GPU; 8 was the fastest for a 2^24-stage stream)
-  int S = segments > 0 ? segments : (int)std::max<int64_t>(1, std::min<int64_t>(8, nb / 1024));
-  S = (int)std::min<int64_t>(std::min<int64_t>(S, kHostMaxSegments), nb);
-  int64_t bps = ceil_div(nb, S);
-  bps += bps & 1;  // whole pairs per segment
-  S = (int)ceil_div(nb, bps);
+  // runs of whole pairs of blocks; automatic: up to 6 runs of at least 1024
+  // blocks.  A run's decode takes at least the dependency chain of one pair
+  // (about half the whole stream's decode time for 4 threads per pair), so
+  // more, shorter runs start sooner but end no sooner; runs with a
+  // different kernel configuration (a shorter chain) slowed the whole call
+  // down, the kernels sharing the SMs badly.
+  int64_t want = segments > 0 ? segments : std::max<int64_t>(1, std::min<int64_t>(6, nb / 1024));
+  want = std::min<int64_t>(std::min<int64_t>(want, kHostMaxSegments), nb);
+  int64_t bps = ceil_div(nb, want);
+  bps += bps & 1;  // whole pairs per run
+  struct Run {
+    int64_t b0, b1;
+  };
+  std::vector<Run> runs;
+  for (int64_t b = 0; b < nb; b += bps) runs.push_back({b, std::min(nb, b + bps)});
+  const int S = (int)runs.size();
+  if (S > kHostMaxSegments) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
   const int64_t jmax = ((int64_t)c->D + c->L + 7) & ~7LL;
   const size_t slice_words = (size_t)jmax * (size_t)(bps / 2) * e.words_per_stage;
@@ -707,10 +787,16 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
   PBVD_CUDA(cudaEventRecord(c->hp_fork, user));
   PBVD_CUDA(cudaStreamWaitEvent(c->hp_copy, c->hp_fork, 0));
   for (int l = 0; l < kHostLanes; ++l) PBVD_CUDA(cudaStreamWaitEvent(c->hp_lane[l], c->hp_fork, 0));
-  // soft values of segment i's own blocks, in order on one copy stream
+  // soft values in order on one copy stream: copy i ends L stages into run
+  // i + 1 (the last stage run i's blocks read), so run i waits for copy i only
+  auto copy_edge = [&](int i) -> size_t {
+    if (i <= 0) return 0;
+    if (i >= S) return n_stages;
+    return std::min(n_stages, (size_t)(runs[i].b0 * c->D + c->L));
+  };
   for (int i = 0; i < S; ++i) {
-    const size_t s0 = (size_t)(i * bps * c->D);
-    const size_t s1 = std::min(n_stages, (size_t)((i + 1) * bps * c->D));
+    const size_t s0 = copy_edge(i);
+    const size_t s1 = copy_edge(i + 1);
     size_t v0 = 0, v1 = 0;
     pbvd_llr_count(c, s0, &v0);
     pbvd_llr_count(c, s1, &v1);
@@ -736,18 +822,17 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
   for (int i = 0; i < S; ++i) {
     const int l = i % kHostLanes;
     cudaStream_t st = c->hp_lane[l];
-    // a block reads L stages beyond its segment: wait for the next copy too
-    PBVD_CUDA(cudaStreamWaitEvent(st, c->hp_in[std::min(i + 1, S - 1)], 0));
-    const int64_t b0 = (int64_t)i * bps, b1 = std::min<int64_t>(nb, b0 + bps);
-    a.b_first = b0;
-    a.n_blocks = b1;
-    a.n_pairs = ceil_div(b1 - b0, 2);
+    PBVD_CUDA(cudaStreamWaitEvent(st, c->hp_in[i], 0));
+    const Run& r = runs[i];
+    a.b_first = r.b0;
+    a.n_blocks = r.b1;
+    a.n_pairs = ceil_div(r.b1 - r.b0, 2);
     a.surv = c->hp_surv + (size_t)l * slice_words;
     a.surv_pairs = a.n_pairs;
     const int64_t grid = ceil_div(a.n_pairs, p.groups);
     PBVD_CUDA(e.launch[0](a, (int)grid, p.cta, p.smem_bytes, st));
-    const size_t o0 = (size_t)(b0 * c->D / 8);
-    const size_t o1 = (std::min(n_stages, (size_t)(b1 * c->D)) + 7) / 8;
+    const size_t o0 = (size_t)(r.b0 * c->D / 8);
+    const size_t o1 = (std::min(n_stages, (size_t)(r.b1 * c->D)) + 7) / 8;
     PBVD_CUDA(cudaMemcpyAsync(h_out + o0, c->hp_out + o0, o1 - o0, cudaMemcpyDeviceToHost, st));
   }
   for (int l = 0; l < kHostLanes; ++l) {
@@ -803,6 +888,8 @@ void pbvd_batch_destroy(pbvd_batch* b) {
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->d_surv) cudaFree(b->d_surv);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  if (b->staged) cudaEventDestroy(b->staged);
   delete b;
 }
 

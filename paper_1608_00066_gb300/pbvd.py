@@ -166,8 +166,9 @@ def pbvd_decode(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0
 
 
 def pbvd_decode_host(ctx: int, h_llr: int, n_stages: int, h_out: int, segments: int = 0, stream: int = 0) -> None:
-    """Host-memory decode with the copies overlapped with decoding (host
-    pointers; page-locked memory for the overlap)."""
+    """Host-memory decode (host pointers).  segments: 0 = copy pipeline with
+    an automatic number of runs of blocks, > 0 = that many runs, -1 = direct
+    access by the kernel (both buffers mapped page-locked memory)."""
     _check(load().pbvd_decode_host(ctx, h_llr, n_stages, h_out, segments, stream), "pbvd_decode_host")
 
 
@@ -350,9 +351,12 @@ class Decoder:
 
 
     def decode_host(self, llr, n_stages: int, out=None, segments: int = 0, stream=None):
-        """llr: int8 CPU tensor (page-locked for overlap) of the sent soft
-        values; returns (or fills) a uint8 CPU tensor of ceil(n_stages / 8)
-        packed bytes, complete once ``stream`` has passed this call."""
+        """llr: int8 CPU tensor of the sent soft values; returns (or fills) a
+        uint8 CPU tensor of ceil(n_stages / 8) packed bytes, complete once
+        ``stream`` has passed this call.  Page-locked tensors (the default
+        ``out`` is one) let the copies overlap the decoding; ``segments`` > 0
+        sets the number of runs of blocks, -1 selects direct access by the
+        kernel (page-locked tensors only)."""
         import torch
         if llr.dtype != torch.int8 or llr.is_cuda or not llr.is_contiguous():
             raise ValueError("llr must be a contiguous int8 CPU tensor")

@@ -245,7 +245,7 @@ def percentiles_us(x: np.ndarray) -> Dict[str, float]:
 class ServeConfig:
     arena_bytes: int = 256 << 20       # device memory for admitted requests
     inflight: int = 3                  # batches in flight (CUDA streams)
-    max_batch_bits: int = 4 << 20      # information bits per batch
+    max_batch_bits: int = 16 << 20     # information bits per batch
     max_batch_items: int = 4096
     max_wait_ms: Optional[float] = 50.0
     reserve_sms: int = 0               # SMs the batch grid leaves to stream pushes

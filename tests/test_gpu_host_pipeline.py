@@ -1,8 +1,9 @@
 """pbvd_decode_host: a stream in host memory, cut into runs of blocks whose
-copies overlap the decoding (Sec. IV-C), must give exactly the bits of
+copies overlap the decoding (Sec. IV-C), or read and written in place by the
+kernel (direct access to page-locked buffers), must give exactly the bits of
 pbvd_decode on the same soft values (and so the block oracle's), for any
-number of runs, ragged last runs, punctured codes, the 256-state code,
-page-locked and pageable host buffers, and calls in a row."""
+number of runs, ragged last runs, direct access, punctured codes, the
+256-state code, page-locked and pageable host buffers, and calls in a row."""
 import numpy as np
 import pytest
 
@@ -46,13 +47,14 @@ def _host_bits(dec, f, segments, pinned=True):
     ("K7_r1/2", 123457, 256, 35),
     ("K7_r3/4", 200001, 512, 42),
     ("K9_r1/3", 100003, 1024, 64),
+    ("K7_r1/2", 140001, 64, 42),    # 2188 blocks: two automatic runs
 ])
 def test_matches_device_decode(name, k, D, L):
     spec = synth.CODES[name]
     f = synth.make_frame(spec, k, 2.0, seed=k)
     dec = make_decoder(spec, D, L)
     want = _device_bits(dec, f)
-    for segments in (0, 1, 2, 3, 7, 64):
+    for segments in (0, -1, 1, 2, 3, 7, 64):
         got = _host_bits(dec, f, segments)
         assert np.array_equal(got, want), segments
     dec.close()
@@ -60,7 +62,8 @@ def test_matches_device_decode(name, k, D, L):
 
 def test_small_and_ragged_against_oracle():
     spec = synth.K7_R12
-    for k, D, L, segments in ((1, 8, 5, 0), (50, 16, 20, 3), (3001, 64, 42, 64), (4000, 512, 42, 5)):
+    for k, D, L, segments in ((1, 8, 5, 0), (50, 16, 20, 3), (3001, 64, 42, 64), (4000, 512, 42, 5),
+                              (2, 8, 5, -1), (777, 16, 20, -1)):
         f = synth.make_frame(spec, k, 1.5, seed=100 + k)
         dec = make_decoder(spec, D, L)
         want = np.packbits(oracle_bits(spec, f.llr, f.n_stages, D, L), bitorder="little")
@@ -77,4 +80,27 @@ def test_pageable_buffers_and_calls_in_a_row():
         want = _device_bits(dec, f)
         assert np.array_equal(_host_bits(dec, f, 0, pinned=False), want)
         assert np.array_equal(_host_bits(dec, f, 6, pinned=True), want)
+    dec.close()
+
+
+def test_direct_access_needs_mapped_buffers():
+    """segments = -1 with a pageable buffer is refused on the host, before
+    anything is enqueued; the copy pipeline takes any mix of buffers."""
+    spec = synth.K7_R12
+    f = synth.make_frame(spec, 5000, 2.0, seed=77)
+    dec = make_decoder(spec, 512, 42)
+    want = _device_bits(dec, f)
+    h = torch.from_numpy(f.llr.copy())
+    out = torch.zeros((f.n_stages + 7) // 8, dtype=torch.uint8)
+    with pytest.raises(pbvd.PbvdError):
+        dec.decode_host(h, f.n_stages, out=out, segments=-1)
+    with pytest.raises(pbvd.PbvdError):
+        dec.decode_host(h.pin_memory(), f.n_stages, out=out, segments=-1)
+    dec.decode_host(h, f.n_stages, out=out, segments=0)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), want)
+    out.zero_()
+    dec.decode_host(h.pin_memory(), f.n_stages, out=out, segments=0)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), want)
     dec.close()
