@@ -252,7 +252,7 @@ def run_ours(args, rank: int, world: int):
     d_out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     if args.tune:
         dec.set_config(**json.loads(args.tune))
-    else:
+    elif args.autotune:
         dec.autotune(d_llr, n, d_out, reps=3)  # kernel configuration, outside the timed region
     cfg = dec.get_config(n)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (~129 MB)
@@ -430,14 +430,19 @@ def run_batched(args):
 
 def run_latency(args):
     """One 4096-bit K=7 r1/2 frame at 3 dB, D=512, L=42: device time of one
-    decode (median over repetitions), tuned kernel configuration."""
+    decode (median over repetitions), the library's automatic kernel
+    configuration (tuned with --autotune)."""
     import torch
     from paper_1608_00066_gb300 import pbvd, synth
     f = synth.make_frame(synth.K7_R12, 4096, 3.0, seed=1001)
     dec = pbvd.Decoder(7, synth.K7_R12.gens, None, 512, 42)
     d = torch.from_numpy(f.llr).cuda()
     o = torch.empty((f.n_stages + 7) // 8, dtype=torch.uint8, device="cuda")
-    cfg, _ = dec.autotune(d, f.n_stages, o, reps=5)
+    if args.autotune:
+        dec.autotune(d, f.n_stages, o, reps=5)
+    cfg = dec.get_config(f.n_stages)
+    for _ in range(5):
+        dec.decode(d, f.n_stages, o)
     ts = []
     for _ in range(50):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -483,7 +488,8 @@ def run_k9(args):
     dec = pbvd.Decoder(spec.K, spec.gens, None, D, L)
     d_llr = torch.from_numpy(f.llr).cuda()
     d_out = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
-    dec.autotune(d_llr, n, d_out, reps=3)
+    if args.autotune:
+        dec.autotune(d_llr, n, d_out, reps=3)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     ms = time_decode(dec, d_llr, n, d_out, max(5, args.steps), max(3, args.warmup), flush)
     bits = np.unpackbits(d_out.cpu().numpy(), bitorder="little")[:K_INFO]
@@ -624,6 +630,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tune", default="", help="JSON kernel config (threads_per_pair, cta_threads, ...)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the kernel configurations first and keep the fastest (default: the library's "
+                         "automatic configuration, the same in every run)")
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and latency extras")
