@@ -104,3 +104,22 @@ def test_direct_access_needs_mapped_buffers():
     torch.cuda.synchronize()
     assert np.array_equal(out.numpy(), want)
     dec.close()
+
+
+def test_two_contexts_in_flight():
+    """Calls on two contexts and two CUDA streams overlap on the GPU (one
+    call's copies with the other's decoding); every output stays exact."""
+    spec = synth.K7_R12
+    frames = [synth.make_frame(spec, 200000 + 1000 * i, 2.5, seed=300 + i) for i in range(6)]
+    decs = [make_decoder(spec, 512, 42) for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    want = [_device_bits(decs[0], f) for f in frames]
+    hins = [torch.from_numpy(f.llr.copy()).pin_memory() for f in frames]
+    outs = [torch.zeros((f.n_stages + 7) // 8, dtype=torch.uint8).pin_memory() for f in frames]
+    for i, f in enumerate(frames):
+        decs[i & 1].decode_host(hins[i], f.n_stages, out=outs[i], stream=streams[i & 1])
+    torch.cuda.synchronize()
+    for i in range(len(frames)):
+        assert np.array_equal(outs[i].numpy(), want[i]), i
+    for d in decs:
+        d.close()
