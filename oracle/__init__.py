@@ -65,6 +65,7 @@ def _load():
             "orc_block_geometry": (None, [I64, I64, I64, I64, P, P, P, P]),
             "orc_viterbi_block_range": (I, [I, I, P, P, I64, I64, I64, I64, I64, P]),
             "orc_viterbi_block": (I, [I, I, P, P, I64, I64, I64, P]),
+            "orc_viterbi_block_metrics": (I, [I, I, P, P, I64, I64, I64, I64, I64, P, P]),
             "orc_viterbi_window": (I, [I, I, P, P, I64, I64, I64, P]),
             "orc_brute_force": (I, [I, I, P, P, I, P, P, P]),
         }
@@ -209,6 +210,25 @@ def viterbi_block(K: int, gens, llr, D: int, L: int, blocks=None) -> np.ndarray:
     if rc != 0:
         raise ValueError("orc_viterbi_block failed (D=%d, L=%d)" % (D, L))
     return out
+
+
+def viterbi_block_metrics(K: int, gens, llr, D: int, L: int, blocks):
+    """Blocks b0..b1-1 of the block-based VA: (bits uint8[n], pm_end int64[b1-b0]).
+
+    pm_end[i] is PM(S_0) after the last forward stage of block b0 + i, the
+    metric of the path its traceback follows."""
+    g = _gens(gens)
+    R = len(g)
+    l = _i8(llr).reshape(-1)
+    n = len(l) // R
+    out = np.zeros(n, dtype=np.uint8)
+    b0, b1 = blocks
+    pm = np.zeros(max(b1 - b0, 1), dtype=np.int64)
+    rc = _load().orc_viterbi_block_metrics(K, R, _ptr(g), _ptr(l), n, D, L, b0, b1,
+                                           _ptr(out), _ptr(pm))
+    if rc != 0:
+        raise ValueError("orc_viterbi_block_metrics failed (D=%d, L=%d)" % (D, L))
+    return out, pm[:b1 - b0].copy()
 
 
 def viterbi_window(K: int, gens, llr, D: int, L: int) -> np.ndarray:

@@ -260,10 +260,13 @@ void orc_block_geometry(int64_t n, int64_t D, int64_t L, int64_t b,
  * own: fresh metrics (known start if the block's range begins at stage 0,
  * all zero otherwise), Eq. (1) over [f0, f1], traceback from S_0 at f1 with
  * no metric comparison, and output of the stages [bD, min((b+1)D, n)).
- * out is indexed by absolute stage.  Returns 0, or -1 on bad arguments or
- * allocation failure. */
-int orc_viterbi_block_range(int K, int R, const uint32_t *gens, const int8_t *llr, int64_t n,
-                            int64_t D, int64_t L, int64_t b_begin, int64_t b_end, uint8_t *out)
+ * out is indexed by absolute stage.  When pm_end is not NULL,
+ * pm_end[b - b_begin] receives PM(S_0) after stage f1: the metric of the path
+ * the traceback follows.  Returns 0, or -1 on bad arguments or allocation
+ * failure. */
+int orc_viterbi_block_metrics(int K, int R, const uint32_t *gens, const int8_t *llr, int64_t n,
+                              int64_t D, int64_t L, int64_t b_begin, int64_t b_end, uint8_t *out,
+                              int64_t *pm_end)
 {
     int v = K - 1;
     uint32_t N = 1u << v;
@@ -288,6 +291,8 @@ int orc_viterbi_block_range(int K, int R, const uint32_t *gens, const int8_t *ll
             orc_acs_stage(K, R, gens, llr + s * R, pm, pm2, dec + (s - f0) * N);
             int64_t *t = pm; pm = pm2; pm2 = t;
         }
+        if (pm_end)
+            pm_end[b - b_begin] = pm[0];
         uint32_t state = 0;
         for (int64_t s = f1; s >= o0; s--) {
             if (s < o1)
@@ -297,6 +302,12 @@ int orc_viterbi_block_range(int K, int R, const uint32_t *gens, const int8_t *ll
     }
     free(pm); free(pm2); free(dec);
     return 0;
+}
+
+int orc_viterbi_block_range(int K, int R, const uint32_t *gens, const int8_t *llr, int64_t n,
+                            int64_t D, int64_t L, int64_t b_begin, int64_t b_end, uint8_t *out)
+{
+    return orc_viterbi_block_metrics(K, R, gens, llr, n, D, L, b_begin, b_end, out, NULL);
 }
 
 int orc_viterbi_block(int K, int R, const uint32_t *gens, const int8_t *llr, int64_t n,
