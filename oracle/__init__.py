@@ -66,6 +66,8 @@ def _load():
             "orc_viterbi_block_range": (I, [I, I, P, P, I64, I64, I64, I64, I64, P]),
             "orc_viterbi_block": (I, [I, I, P, P, I64, I64, I64, P]),
             "orc_viterbi_block_metrics": (I, [I, I, P, P, I64, I64, I64, I64, I64, P, P]),
+            "orc_viterbi_block_variant": (I, [I, I, P, P, I64, I64, I64, I64, I64, I, P, P]),
+            "orc_encode_tailbiting": (I64, [I, I, P, P, I64, P]),
             "orc_viterbi_window": (I, [I, I, P, P, I64, I64, I64, P]),
             "orc_brute_force": (I, [I, I, P, P, I, P, P, P]),
         }
@@ -229,6 +231,41 @@ def viterbi_block_metrics(K: int, gens, llr, D: int, L: int, blocks):
     if rc != 0:
         raise ValueError("orc_viterbi_block_metrics failed (D=%d, L=%d)" % (D, L))
     return out, pm[:b1 - b0].copy()
+
+
+TB_ARGMIN = 1
+CIRCULAR = 2
+
+
+def viterbi_block_variant(K: int, gens, llr, D: int, L: int, argmin: bool = False,
+                          circular: bool = False, blocks=None):
+    """Block form with the argmin traceback start (Sec. II's S_E) and/or
+    circular (tail-biting) windows; returns (bits uint8[n], pm_end int64[])."""
+    g = _gens(gens)
+    R = len(g)
+    l = _i8(llr).reshape(-1)
+    n = len(l) // R
+    nb = (n + D - 1) // D
+    b0, b1 = blocks if blocks is not None else (0, nb)
+    out = np.zeros(n, dtype=np.uint8)
+    pm = np.zeros(max(b1 - b0, 1), dtype=np.int64)
+    flags = (TB_ARGMIN if argmin else 0) | (CIRCULAR if circular else 0)
+    rc = _load().orc_viterbi_block_variant(K, R, _ptr(g), _ptr(l), n, D, L, b0, b1, flags,
+                                           _ptr(out), _ptr(pm))
+    if rc != 0:
+        raise ValueError("orc_viterbi_block_variant failed (D=%d, L=%d)" % (D, L))
+    return out, pm[:b1 - b0].copy()
+
+
+def encode_tailbiting(K: int, gens, msg) -> np.ndarray:
+    """Tail-biting encoding (start state = end state); (k, R) uint8, k >= K-1."""
+    g = _gens(gens)
+    m = np.ascontiguousarray(np.asarray(msg, dtype=np.uint8))
+    R = len(g)
+    out = np.zeros(len(m) * R, dtype=np.uint8)
+    if _load().orc_encode_tailbiting(K, R, _ptr(g), _ptr(m), len(m), _ptr(out)) < 0:
+        raise ValueError("tail-biting frames need k >= K - 1")
+    return out.reshape(len(m), R)
 
 
 def viterbi_window(K: int, gens, llr, D: int, L: int) -> np.ndarray:

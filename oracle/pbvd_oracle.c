@@ -31,6 +31,10 @@
  *   orc_depuncture      puncturing is not in the paper; punctured positions
  *                       are read as erasures (LLR 0), which add the same
  *                       amount to every branch metric.
+ *   orc_viterbi_block_variant  the block form with the argmin start state
+ *                       of the classic VA (Sec. II) and/or circular windows
+ *                       for tail-biting frames (not in the paper);
+ *   orc_encode_tailbiting  tail-biting encoder (start state = end state);
  *   orc_viterbi_window  continuous (carried-metric) form for streaming:
  *                       Eq. (1) run without restarts over an unbounded stream;
  *                       each segment of D stages is released once L further
@@ -308,6 +312,95 @@ int orc_viterbi_block_range(int K, int R, const uint32_t *gens, const int8_t *ll
                             int64_t D, int64_t L, int64_t b_begin, int64_t b_end, uint8_t *out)
 {
     return orc_viterbi_block_metrics(K, R, gens, llr, n, D, L, b_begin, b_end, out, NULL);
+}
+
+/* Variants of the block form (Sec. III-A) selected by flags:
+ *   ORC_TB_ARGMIN  the traceback of every block starts from the state with
+ *                  the smallest metric at f1 (the start state S_E of the
+ *                  classic VA, Sec. II), the lowest state index on ties,
+ *                  instead of S_0;
+ *   ORC_CIRCULAR   tail-biting frames (not in the paper): the frame is a
+ *                  circle of n stages, stage s reads the soft values of stage
+ *                  s mod n; block b's window is [o0 - L, o1 + L - 1] with no
+ *                  clamping and every block starts from zero metrics (the
+ *                  encoder's start state is unknown).
+ * With flags = 0 this is orc_viterbi_block_metrics.  pm_end (optional)
+ * receives the metric of the traceback's start state per block. */
+#define ORC_TB_ARGMIN 1
+#define ORC_CIRCULAR 2
+
+int orc_viterbi_block_variant(int K, int R, const uint32_t *gens, const int8_t *llr, int64_t n,
+                              int64_t D, int64_t L, int64_t b_begin, int64_t b_end, int flags,
+                              uint8_t *out, int64_t *pm_end)
+{
+    int v = K - 1;
+    uint32_t N = 1u << v;
+    int circular = (flags & ORC_CIRCULAR) != 0;
+    if (D <= 0 || L < 0)
+        return -1;
+    if (n <= 0)
+        return 0;
+    int64_t span = D + 2 * L;
+    int64_t *pm = (int64_t *)malloc(sizeof(int64_t) * N);
+    int64_t *pm2 = (int64_t *)malloc(sizeof(int64_t) * N);
+    uint8_t *dec = (uint8_t *)malloc((size_t)span * N);
+    if (!pm || !pm2 || !dec) {
+        free(pm); free(pm2); free(dec);
+        return -1;
+    }
+    for (int64_t b = b_begin; b < b_end; b++) {
+        int64_t f0, f1, o0, o1;
+        orc_block_geometry(n, D, L, b, &f0, &f1, &o0, &o1);
+        if (circular) {
+            f0 = o0 - L;
+            f1 = o1 + L - 1;
+        }
+        int known = !circular && f0 == 0;
+        for (uint32_t j = 0; j < N; j++)
+            pm[j] = known ? (j == 0 ? 0 : ORC_BIG) : 0;
+        for (int64_t s = f0; s <= f1; s++) {
+            int64_t sm = ((s % n) + n) % n;
+            orc_acs_stage(K, R, gens, llr + sm * R, pm, pm2, dec + (s - f0) * N);
+            int64_t *t = pm; pm = pm2; pm2 = t;
+        }
+        uint32_t state = 0;
+        if (flags & ORC_TB_ARGMIN) {
+            for (uint32_t j = 1; j < N; j++)
+                if (pm[j] < pm[state])
+                    state = j;
+        }
+        if (pm_end)
+            pm_end[b - b_begin] = pm[state];
+        for (int64_t s = f1; s >= o0; s--) {
+            if (s < o1)
+                out[s] = (uint8_t)orc_state_bit(K, state);
+            state = orc_predecessor(K, state, dec[(s - f0) * N + state]);
+        }
+    }
+    free(pm); free(pm2); free(dec);
+    return 0;
+}
+
+/* Tail-biting encoding (not in the paper): the encoder starts in the state
+ * its last v message bits leave it in, so that it ends where it started; k
+ * stages, no tail.  Needs k >= v.  out as for orc_encode. */
+int64_t orc_encode_tailbiting(int K, int R, const uint32_t *gens, const uint8_t *msg, int64_t k,
+                              uint8_t *out)
+{
+    int v = K - 1;
+    if (k < v)
+        return -1;
+    uint32_t d = 0;
+    for (int64_t s = k - v; s < k; s++)
+        d = orc_next_state(K, d, msg[s] & 1);
+    for (int64_t s = 0; s < k; s++) {
+        int x = msg[s] & 1;
+        uint32_t c = orc_codeword(K, R, gens, d, x);
+        for (int r = 0; r < R; r++)
+            out[s * R + r] = (uint8_t)((c >> (R - 1 - r)) & 1u);
+        d = orc_next_state(K, d, x);
+    }
+    return k;
 }
 
 int orc_viterbi_block(int K, int R, const uint32_t *gens, const int8_t *llr, int64_t n,

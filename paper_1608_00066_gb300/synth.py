@@ -96,6 +96,23 @@ def conv_encode(spec: CodeSpec, msg: np.ndarray) -> np.ndarray:
     return out
 
 
+def conv_encode_tailbiting(spec: CodeSpec, msg: np.ndarray) -> np.ndarray:
+    """Tail-biting encoding as a circular convolution over GF(2): code bit r
+    of stage s is sum_i h_i m[(s - i) mod k] (the encoder starts in the state
+    its last K-1 message bits leave it in, and ends there).  (k, R) uint8."""
+    m = np.asarray(msg, dtype=np.int64)
+    k = len(m)
+    out = np.zeros((k, spec.R), dtype=np.uint8)
+    for r, g in enumerate(spec.gens):
+        h = taps(g, spec.K).astype(np.int64)
+        acc = np.zeros(k, dtype=np.int64)
+        for i in range(spec.K):
+            if h[i]:
+                acc ^= np.roll(m, i)
+        out[:, r] = acc & 1
+    return out
+
+
 def puncture_bits(spec: CodeSpec, coded: np.ndarray) -> np.ndarray:
     """(n, R) code bits -> 1-D sent bits in stage-major, r-ascending order."""
     if spec.puncture is None:
@@ -147,16 +164,34 @@ def make_frame(spec: CodeSpec, k: int, ebn0_db: Optional[float], seed) -> Frame:
     return Frame(spec, msg, llr, k + spec.v, float("inf") if ebn0_db is None else ebn0_db)
 
 
+def make_tailbiting_frame(spec: CodeSpec, k: int, ebn0_db: Optional[float], seed) -> Frame:
+    """A tail-biting frame of k random message bits (k stages, no tail);
+    ``ebn0_db=None`` gives error-free soft values.  Unpunctured codes only."""
+    if spec.puncture is not None:
+        raise ValueError("tail-biting frames are built for unpunctured codes")
+    rng = np.random.default_rng(seed)
+    msg = rng.integers(0, 2, size=k, dtype=np.uint8)
+    sent = conv_encode_tailbiting(spec, msg).reshape(-1)
+    if ebn0_db is None:
+        llr = noiseless_int8(sent)
+    else:
+        llr = bpsk_awgn_int8(rng, sent, ebn0_db, spec.rate)
+    return Frame(spec, msg, llr, k, float("inf") if ebn0_db is None else ebn0_db)
+
+
+def batch_frame(f: int, seed: int, k_range=(40, 6144), ebn0_range=(1.0, 5.0),
+                codes: Sequence[CodeSpec] = (K7_R12, K7_R34, K9_R13)) -> Frame:
+    """Frame f of a mixed-code batch: info length ~ U{k_lo..k_hi}, code uniform
+    over ``codes``, Eb/N0 ~ U[lo, hi] dB, all drawn from SeedSequence([seed, f])."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, f]))
+    k = int(rng.integers(k_range[0], k_range[1] + 1))
+    spec = codes[int(rng.integers(0, len(codes)))]
+    eb = float(rng.uniform(ebn0_range[0], ebn0_range[1]))
+    sub = int(rng.integers(0, 2 ** 63 - 1))
+    return make_frame(spec, k, eb, sub)
+
+
 def batch_frames(n_frames: int, seed: int, k_range=(40, 6144), ebn0_range=(1.0, 5.0),
                  codes: Sequence[CodeSpec] = (K7_R12, K7_R34, K9_R13)):
-    """Mixed-code batch: info length ~ U{k_lo..k_hi}, code uniform over
-    ``codes``, Eb/N0 ~ U[lo, hi] dB; frame f draws from SeedSequence([seed, f])."""
-    frames = []
-    for f in range(n_frames):
-        rng = np.random.default_rng(np.random.SeedSequence([seed, f]))
-        k = int(rng.integers(k_range[0], k_range[1] + 1))
-        spec = codes[int(rng.integers(0, len(codes)))]
-        eb = float(rng.uniform(ebn0_range[0], ebn0_range[1]))
-        sub = int(rng.integers(0, 2 ** 63 - 1))
-        frames.append(make_frame(spec, k, eb, sub))
-    return frames
+    """Mixed-code batch of n_frames frames (see batch_frame)."""
+    return [batch_frame(f, seed, k_range, ebn0_range, codes) for f in range(n_frames)]
