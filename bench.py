@@ -50,12 +50,31 @@ def algorithmic_ops_per_bit(N: int, D: int, L: int) -> float:
     return 3.0 * N * (D + 2 * L) / D
 
 
-# DRAM bytes (read + write) of one launch of the stream decode kernel, from
-# the ncu capture summarised in profiles/pbvd_decode_k7_stream_2e24.md, keyed
-# by kernel configuration (threads per pair, CTA threads, survivors in
-# shared memory).  Reported only when the timed launch used that
-# configuration; a change to the kernel invalidates it.
-PROFILED_TRAFFIC = {(4, 64, 0): 124055808 + 127864832}
+# DRAM bytes (read + write) of one launch of the stream decode kernel from
+# one ncu capture of the benchmark's workload, keyed by kernel configuration
+# (threads per pair, CTA threads, survivors in shared memory) and tied to a
+# hash of the device sources it was captured with: reported only when the
+# timed launch used that configuration and the sources are unchanged, else
+# null (the counters no longer describe the kernel).
+PROFILED_TRAFFIC = {(4, 64, 0): {"bytes": 124055808 + 127864832, "sources": None}}
+
+
+def kernel_sources_hash() -> str:
+    """sha256 (16 hex digits) of the decode kernel's device sources."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1608_00066_gb300", "csrc")
+    for name in ("pbvd_device.cuh", "pbvd_warp.cuh", "pbvd_internal.h", "pbvd_instances.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(key):
+    rec = PROFILED_TRAFFIC.get(key)
+    if not rec or rec["sources"] != kernel_sources_hash():
+        return None
+    return rec["bytes"]
 
 
 def hbm_peak_gbs() -> tuple:
@@ -68,10 +87,25 @@ def hbm_peak_gbs() -> tuple:
         return 6800.0, "fallback"
 
 
+def device_sm_count(default: int = 152) -> int:
+    try:
+        import torch
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        return default
+
+
 def peak_int16_ops(sm_count: int = 152, clock_hz: float = 2.07e9) -> float:
     """Issue-limited integer peak: 4 schedulers x 32 lanes per SM per clock,
     two 16-bit operations per lane (packed 16x2 arithmetic)."""
     return sm_count * 4 * 32 * 2 * clock_hz
+
+
+def peak_source(sm_count: int, mhz: float) -> str:
+    return ("issue limit: %d SMs (device) x 4 schedulers x 32 lanes x 2 (16x2) x %.0f MHz (the SM clock's "
+            "maximum as sampled); the ALU pipe alone issues half of that (64 lanes/clk/SM, measured), "
+            "and the kernels place part of their adds on the FMA pipe, so the issue limit is the "
+            "ceiling" % (sm_count, mhz))
 
 
 # ------------------------------------------------------------------ clocks
@@ -160,32 +194,32 @@ def _oracle_worker(args):
     llr_path, K, gens, n, D, L, b0, b1 = args
     sys.path.insert(0, ROOT)
     import oracle as orc
-    llr = np.load(llr_path, mmap_mode="r").reshape(n, 2)
+    llr = np.load(llr_path, mmap_mode="r").reshape(n, len(gens))
     t0 = time.perf_counter()
     orc.viterbi_block(K, gens, llr, D, L, blocks=(b0, b1))
     dt = time.perf_counter() - t0
     return 0, dt, int(min(b1 * D, n) - b0 * D)
 
 
-def cpu_oracle_rate(llr: np.ndarray, n: int, target_s: float = 15.0, max_cores=None):
+def cpu_oracle_rate(llr: np.ndarray, n: int, target_s: float = 15.0, max_cores=None, K: int = 7,
+                    gens=(0o171, 0o133), D: int = D_BLOCK, L: int = L_OVERLAP):
     """Times the block-based CPU oracle on a bounded sample of the stream's
-    blocks spread over all host cores (spawned processes); returns Mb/s of
-    decoded information bits and a description."""
+    blocks spread over the host cores (spawned processes; max_cores = 1: one
+    core); returns Gb/s of decoded information bits and a description."""
     import multiprocessing as mp
     import tempfile
     import oracle as orc
     orc.build()
     cores = max_cores or os.cpu_count() or 1
-    nb = (n + D_BLOCK - 1) // D_BLOCK
+    nb = (n + D - 1) // D
     tmp = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
     tmp.close()
     np.save(tmp.name, llr)
-    gens = (0o171, 0o133)
     ctx = mp.get_context("spawn")
     try:
         with ctx.Pool(cores) as pool:
             # calibrate: one block per core
-            cal = pool.map(_oracle_worker, [(tmp.name, 7, gens, n, D_BLOCK, L_OVERLAP, 1 + c, 2 + c)
+            cal = pool.map(_oracle_worker, [(tmp.name, K, gens, n, D, L, 1 + c, 2 + c)
                                             for c in range(cores)])
             per_block = max(1e-4, statistics.median(r[1] for r in cal))
             blocks_per_core = max(1, int(target_s / per_block))
@@ -193,7 +227,7 @@ def cpu_oracle_rate(llr: np.ndarray, n: int, target_s: float = 15.0, max_cores=N
             jobs = []
             for c in range(cores):
                 b0 = 1 + c * blocks_per_core
-                jobs.append((tmp.name, 7, gens, n, D_BLOCK, L_OVERLAP, b0, b0 + blocks_per_core))
+                jobs.append((tmp.name, K, gens, n, D, L, b0, b0 + blocks_per_core))
             t0 = time.perf_counter()
             res = pool.map(_oracle_worker, jobs)
             wall = time.perf_counter() - t0
@@ -205,6 +239,24 @@ def cpu_oracle_rate(llr: np.ndarray, n: int, target_s: float = 15.0, max_cores=N
     return {"value": bits / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of %d blocks (%d info bits), %d spawned processes, %.1f s wall"
                       % (cores * blocks_per_core, nb, bits, cores, wall)}
+
+
+def cpu_other_configs():
+    """The CPU oracle on the single 4096-bit K=7 frame (whole frame, one core)
+    and on a sample of the K=9 r1/3 2^24-bit stream (all cores)."""
+    import oracle as orc
+    from paper_1608_00066_gb300 import synth
+    f = synth.make_frame(synth.K7_R12, 4096, 3.0, seed=1001)
+    reps = 20
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        orc.viterbi_block(7, synth.K7_R12.gens, f.llr.reshape(-1, 2), 512, 42)
+    dt = (time.perf_counter() - t0) / reps
+    k9 = synth.make_frame(synth.K9_R13, K_INFO, 2.0, seed=3001)
+    r9 = cpu_oracle_rate(k9.llr, k9.n_stages, target_s=6.0, K=9, gens=synth.K9_R13.gens, D=1024, L=64)
+    return {"frame_4096_k7": {"value": 4096 / dt / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": "whole frame (9 blocks), mean of %d decodes" % reps},
+            "k9_r13_stream": r9}
 
 
 # -------------------------------------------------------------- our arm
@@ -357,16 +409,26 @@ def run_ours(args, rank: int, world: int):
     ms, e2e_ms, e2e_direct_ms, e2e_stream_ms = max_over_ranks([ms, e2e_ms, e2e_direct_ms, e2e_stream_ms], world)
 
     batched = run_batched(args) if (rank == 0 and not args.no_batch) else None
+    batched_k7 = None
+    if rank == 0 and not args.no_batch:
+        from paper_1608_00066_gb300 import synth as _s
+        batched_k7 = run_batched(args, codes=(_s.K7_R12,), seed=4003,
+                                 label="10,000 K7 r1/2 (171,133) frames, k ~ U[40,6144], Eb/N0 ~ U[1,5] dB")
+    two_kernel = run_two_kernel(args, dec, d_llr, n, d_out, flush, ms) if rank == 0 else None
+    quant = run_quantised(args, dec, stream, flush) if (rank == 0 and not args.no_batch) else None
     latency = run_latency(args) if (rank == 0 and not args.no_batch) else None
     k9 = run_k9(args) if (rank == 0 and not args.no_batch) else None
 
     value = aggregate_gbps(K_INFO, world, ms)
     e2e = aggregate_gbps(K_INFO, world, e2e_ms)
     ops = algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP) * K_INFO
-    peak = peak_int16_ops()
+    clocks = clk.summary()
+    sms = device_sm_count()
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = peak_int16_ops(sms, max_mhz * 1e6)
     achieved = ops / (ms * 1e-3)
     key = (cfg["threads_per_pair"], cfg["cta_threads"], cfg["survivors_in_smem"])
-    traffic = args.traffic if args.traffic is not None else PROFILED_TRAFFIC.get(key)
+    traffic = args.traffic if args.traffic is not None else profiled_traffic(key)
     hbm_peak, hbm_src = hbm_peak_gbs()
     alg_bytes = int(frame.llr.nbytes) + nbytes
     result = {
@@ -381,7 +443,8 @@ def run_ours(args, rank: int, world: int):
                      "unit": "Tops/s (int16)", "frac": round(achieved / peak, 4),
                      "ops_per_bit": round(algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP), 2),
                      "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "peak_source": "issue limit: 152 SMs x 4 schedulers x 32 lanes x 2 (16x2) x 2.07 GHz"},
+                     "peak_source": peak_source(sms, max_mhz),
+                     "kernel_sources": kernel_sources_hash()},
         "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / (ms * 1e-3) / 1e9, 1),
                          "peak": hbm_peak, "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                          "algorithmic_bytes": alg_bytes, "peak_source": hbm_src},
@@ -397,9 +460,12 @@ def run_ours(args, rank: int, world: int):
                               "steps alternating (one call's copies overlap the other's decoding)"},
                 "l2": "flushed before each step (streaming: before the first)"},
         "gpu_launches": args.steps,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "ber": ber,
         "batched_vs_plain": batched,
+        "batched_vs_plain_k7": batched_k7,
+        "two_kernel_ablation": two_kernel,
+        "quantised_inputs": quant,
         "latency": latency,
         "k9_stream": k9,
         "paper_context": PAPER_CONTEXT,
@@ -407,16 +473,35 @@ def run_ours(args, rank: int, world: int):
     return result, frame
 
 
-def run_batched(args):
+def batch_ops(frames, choice) -> float:
+    """Algorithmic integer operations of a batch: 3N per forward stage of every
+    block (Sec. III-A geometry), with each frame's (D, L)."""
+    total = 0.0
+    for f in frames:
+        D, L = choice[f.spec.name]
+        n = f.n_stages
+        nb = (n + D - 1) // D
+        fwd = 0
+        for b in range(nb):
+            f0, f1 = max(0, b * D - L), min(n, (b + 1) * D + L) - 1
+            fwd += f1 - f0 + 1
+        total += 3.0 * (1 << (f.spec.K - 1)) * fwd
+    return total
+
+
+def run_batched(args, codes=None, seed=4001, label=None):
     """Batched workload: 10,000 terminated frames, info lengths uniform in
-    [40, 6144], code drawn per frame from K=7 r1/2, K=7 r3/4 ([110;101]) and
-    K=9 r1/3, Eb/N0 uniform in [1, 5] dB.  D per code is tuned (L = 42 for
-    K=7, 64 for K=9); the batch is one persistent launch replayed from a CUDA
-    graph; plain = one pbvd_decode launch per frame with the same (D, L), so
-    the same bits."""
+    [40, 6144], code drawn per frame from ``codes`` (default K=7 r1/2, K=7 r3/4
+    ([110;101]) and K=9 r1/3), Eb/N0 uniform in [1, 5] dB.  D per code is tuned
+    (L = 42 for K=7, 64 for K=9); the batch is one persistent launch replayed
+    from a CUDA graph; plain = one pbvd_decode launch per frame with the same
+    (D, L), so the same bits and the same BER."""
     import torch
     from paper_1608_00066_gb300 import pbvd, synth, tune
-    frames = synth.batch_frames(10000, seed=4001)
+    if codes is None:
+        frames = synth.batch_frames(10000, seed=seed)
+    else:
+        frames = synth.batch_frames(10000, seed=seed, codes=codes)
     bits = int(sum(len(f.msg) for f in frames))
     flat = np.concatenate([f.llr for f in frames])
     d_all = torch.from_numpy(flat).cuda()
@@ -461,11 +546,24 @@ def run_batched(args):
     ms_p = e0.elapsed_time(e1)
     same = bool(torch.equal(ref, outs))
     pbvd.pbvd_batch_destroy(b)
-    return {"workload": "10,000 mixed-code frames (K7 r1/2, K7 r3/4, K9 r1/3), k ~ U[40,6144], Eb/N0 ~ U[1,5] dB",
+    got = outs.cpu().numpy()
+    errs, off = 0, 0
+    for f in frames:
+        nb_ = (f.n_stages + 7) // 8
+        errs += int((np.unpackbits(got[off:off + nb_], bitorder="little")[:len(f.msg)] != f.msg).sum())
+        off += nb_
+    ops = batch_ops(frames, choice)
+    peak = peak_int16_ops(device_sm_count())
+    return {"workload": label or ("10,000 mixed-code frames (K7 r1/2, K7 r3/4, K9 r1/3), k ~ U[40,6144], "
+                                  "Eb/N0 ~ U[1,5] dB"),
             "info_bits": bits, "geometry": {k: list(v) for k, v in choice.items()},
             "batched_gbps": round(bits / ms_b / 1e6, 3), "batched_ms": round(ms_b, 4),
             "plain_gbps": round(bits / ms_p / 1e6, 4), "plain_ms": round(ms_p, 2),
-            "plain_launches": len(items), "identical_bits": same}
+            "plain_launches": len(items), "identical_bits": same, "ber": errs / bits,
+            "roofline": {"bound": "alu", "achieved": round(ops / (ms_b * 1e-3) / 1e12, 3),
+                         "peak": round(peak / 1e12, 3), "unit": "Tops/s (int16)",
+                         "frac": round(ops / (ms_b * 1e-3) / peak, 4), "ops": ops,
+                         "ops_rule": "3N per forward stage of every block, each frame's own (D, L)"}}
 
 
 def run_latency(args):
@@ -494,6 +592,79 @@ def run_latency(args):
     ts.sort()
     return {"workload": "one K7 r1/2 frame, 4096 info bits, D=512 L=42", "kernel_config": cfg,
             "p50_us": round(1000 * ts[len(ts) // 2], 1), "p99_us": round(1000 * ts[int(len(ts) * 0.99) - 1], 1)}
+
+
+def _event_ms(fn, steps: int, warmup: int, flush, stream):
+    """Mean device time (ms) of fn() over steps calls, L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    pairs = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        pairs.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in pairs) / len(pairs)
+
+
+def run_two_kernel(args, dec, d_llr, n, d_out, flush, fused_ms):
+    """The paper's two-kernel design (Algorithm 1, Table 1: K1 forward with
+    N_c threads per block of stages, PM[N][32] in shared memory and
+    SP[D+2L][N_c][N_t] in global memory; K2 one thread per block) on the
+    headline stream, timed like the fused kernel; its bits must equal the
+    fused kernel's (d_out holds them)."""
+    import torch
+    from paper_1608_00066_gb300 import pbvd
+    stream = torch.cuda.current_stream()
+    out2 = torch.empty_like(d_out)
+
+    def call():
+        pbvd.pbvd_decode_two_kernel(dec.ctx, d_llr.data_ptr(), n, out2.data_ptr(), stream.cuda_stream)
+
+    ms = _event_ms(call, max(5, args.steps), max(3, args.warmup), flush, stream)
+    same = bool(torch.equal(out2, d_out))
+    ops = algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP) * K_INFO
+    return {"workload": WORKLOAD, "design": "paper Algorithm 1: K1 (N_c = 4 threads per block of stages, "
+            "32 blocks per CTA, PM[64][32] in shared memory, survivor words SP[D+2L][N_c][N_t] in global "
+            "memory) + K2 (one thread per block)", "gbps": round(K_INFO / ms / 1e6, 3), "ms": round(ms, 4),
+            "fused_ms": round(fused_ms, 4), "fused_speedup": round(ms / fused_ms, 2),
+            "roofline_frac": round(ops / (ms * 1e-3) / peak_int16_ops(device_sm_count()), 4),
+            "identical_bits": same, "gpu_launches_per_step": 2,
+            "paper_context_Sk_Mbps": {"GTX980": 2122.7, "GTX580": 641.8}}
+
+
+def run_quantised(args, dec, stream, flush):
+    """Sec. IV-C's q-bit input packing: the headline stream (same message and
+    noise, 3 dB) quantised to q bits per soft value (q = 1: hard decisions),
+    floor(32/q) values per 32-bit word.  Device decode of the packed words
+    (unpack + decode) and host-memory decode through the copy pipeline (the
+    packed words cross the host link), with the BER of each q."""
+    import torch
+    from paper_1608_00066_gb300 import synth
+    rows = []
+    for q in (8, 4, 3, 1):
+        f = synth.make_packed_frame(synth.K7_R12, K_INFO, EBN0_DB, q, seed=SEED)
+        n = f.n_stages
+        w_host = torch.from_numpy(f.words.view(np.int32).copy()).pin_memory()
+        w_dev = w_host.cuda()
+        o_dev = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        o_host = torch.empty((n + 7) // 8, dtype=torch.uint8).pin_memory()
+        dev_ms = _event_ms(lambda: dec.decode_packed(w_dev, q, n, out=o_dev, stream=stream),
+                           max(5, args.steps), max(3, args.warmup), flush, stream)
+        host_ms = _event_ms(lambda: dec.decode_packed(w_host, q, n, out=o_host, stream=stream),
+                            max(5, args.steps), max(3, args.warmup), flush, stream)
+        bits_dev = np.unpackbits(o_dev.cpu().numpy(), bitorder="little")[:K_INFO]
+        bits_host = np.unpackbits(o_host.numpy(), bitorder="little")[:K_INFO]
+        rows.append({"q": q, "values_per_word": 32 // q, "h2d_bytes_per_step": int(f.words.nbytes),
+                     "device_gbps": round(K_INFO / dev_ms / 1e6, 3), "e2e_gbps": round(K_INFO / host_ms / 1e6, 3),
+                     "ber": float((bits_dev != f.msg).mean()),
+                     "host_equals_device": bool(np.array_equal(bits_dev, bits_host))})
+    return {"workload": "K7 r1/2 stream, 2^24 info bits, 3 dB, D=512 L=42; q-bit soft values packed "
+                        "floor(32/q) per word (q = 1: hard decision)", "rows": rows}
 
 
 def time_decode(dec, d_llr, n, d_out, steps: int, warmup: int, flush):
@@ -539,7 +710,8 @@ def run_k9(args):
     dec.close()
     return {"workload": "K9 r1/3 (557,663,711) terminated stream, 2^24 info bits, Eb/N0 2 dB, D=1024 L=64",
             "gbps": round(K_INFO / ms / 1e6, 3), "ms": round(ms, 4), "kernel_config": cfg,
-            "ops_per_bit": ops_bit, "roofline_frac": round(achieved / peak_int16_ops(), 4),
+            "ops_per_bit": ops_bit,
+            "roofline_frac": round(achieved / peak_int16_ops(device_sm_count()), 4),
             "ber": float((bits != f.msg).mean())}
 
 
@@ -701,6 +873,9 @@ def main():
         result["serving"] = run_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_oracle_rate(frame.llr, frame.n_stages)
+        result["cpu_baseline"]["single_core"] = cpu_oracle_rate(frame.llr, frame.n_stages, target_s=8.0,
+                                                                max_cores=1)
+        result["cpu_baseline"]["other_configs"] = cpu_other_configs()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -83,6 +83,34 @@ enum {
 PBVD_API int pbvd_create(pbvd_ctx **out, int K, int R, const uint32_t *gens,
                 const uint8_t *puncture, int P, int D, int L);
 
+/* Decoding variants of a context (flags, 0 = the scheme of Sec. III-A):
+ *   PBVD_MODE_ARGMIN      every block's traceback starts from the state with
+ *                         the smallest path metric at its last forward stage
+ *                         (the start state S_E of the classic VA, Sec. II;
+ *                         the lowest state index on ties) instead of S_0;
+ *                         suits streams that are not zero-terminated
+ *   PBVD_MODE_TAILBITING  frames are tail-biting (not in the paper: the
+ *                         encoder starts in the state its last K-1 message
+ *                         bits leave it in; n stages, no tail): the frame is
+ *                         read as a circle, block b's window is
+ *                         [bD - L, min((b+1)D, n) + L - 1] with stage s taken
+ *                         at s mod n, and every block starts from zero metrics
+ *                         (no known start).  pbvd_decode then keeps a copy of
+ *                         the frame with L wrapped stages on each side in a
+ *                         buffer owned by the context (grown on first use of a
+ *                         larger size).  Unpunctured codes only
+ *                         (PBVD_EUNSUPPORTED otherwise).
+ * The flags apply to pbvd_decode, pbvd_decode_packed and pbvd_autotune;
+ * pbvd_decode_host and pbvd_decode_noalloc support PBVD_MODE_ARGMIN only;
+ * batches and streams support neither (PBVD_EUNSUPPORTED).  PBVD_EINVAL for
+ * unknown flags. */
+#define PBVD_MODE_ARGMIN 1
+#define PBVD_MODE_TAILBITING 2
+PBVD_API int pbvd_set_mode(pbvd_ctx *ctx, int flags);
+
+/* Reads the flags set by pbvd_set_mode. */
+PBVD_API int pbvd_get_mode(const pbvd_ctx *ctx, int *flags);
+
 /* Frees the context and its workspace.  Synchronises the device first if
  * work may still be in flight.  NULL is ignored. */
 PBVD_API void pbvd_destroy(pbvd_ctx *ctx);
@@ -100,6 +128,19 @@ PBVD_API void pbvd_destroy(pbvd_ctx *ctx);
  * once with the largest size before capturing a CUDA graph. */
 PBVD_API int pbvd_decode(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
                 uint8_t *d_out, void *stream);
+
+/* The paper's own two-kernel design (Sec. IV-A/IV-B, Algorithm 1, Table 1),
+ * kept as an ablation of pbvd_decode: kernel K1 runs the forward procedure
+ * with N_c threads per block of stages (one per group of butterflies sharing a
+ * codeword alpha, Table 2), 32 blocks per thread block, path metrics in shared
+ * memory laid out PM[N][32], and writes bit-packed survivor words to global
+ * memory laid out SP[D+2L][N_c][N_t]; kernel K2 traces back with one thread
+ * per block.  Same arguments, geometry and bits as pbvd_decode (32-bit path
+ * metrics).  Built for the unpunctured K=7 (171,133) and K=9 (557,663,711)
+ * codes and the plain mode (PBVD_EUNSUPPORTED otherwise).  The survivor
+ * words live in the context workspace, (D+2L) N_c ceil(n_stages/D) words. */
+PBVD_API int pbvd_decode_two_kernel(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages, uint8_t *d_out,
+                                    void *stream);
 
 /* Decodes a stream held in HOST memory, in one of two ways.
  * Copy pipeline (segments >= 0), after the multi-stream scheme of Sec. IV-C
@@ -139,6 +180,33 @@ PBVD_API int pbvd_decode(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
  * GPU. */
 PBVD_API int pbvd_decode_host(pbvd_ctx *ctx, const int8_t *h_llr, size_t n_stages,
                               uint8_t *h_out, int segments, void *stream);
+
+/* Decodes soft values quantised to q bits and packed, as Sec. IV-C stores
+ * them to shrink the input transfer (U_1 = 4R / floor(32/q) bytes per stage
+ * instead of R): floor(32/q) values per 32-bit word, value i in word i / m
+ * (m = floor(32/q)) at bits [q (i mod m), q (i mod m) + q) as a q-bit two's
+ * complement number; q = 1 is hard decision (bit 1 = received code bit 1).
+ *   d_words    device, ceil(count / m) words, count = pbvd_llr_count(n_stages)
+ *              values in the order of pbvd_decode's d_llr (punctured codes:
+ *              the sent values only)
+ *   q          1..8
+ * The branch metric is that of the paper with mu = +-Q, Q = 2^{q-1} - 1
+ * (Q = 1 for q = 1: twice the Hamming distance); values below -Q read as -Q.
+ * The values are unpacked on the device into a buffer owned by the context
+ * (grown on first use of a larger size, a synchronising allocation), scaled
+ * by floor(127 / Q) -- which changes every branch metric of a stage by the
+ * same positive-affine map and therefore no decision -- and decoded as by
+ * pbvd_decode.  d_out as for pbvd_decode. */
+PBVD_API int pbvd_decode_packed(pbvd_ctx *ctx, const uint32_t *d_words, int q, size_t n_stages,
+                                uint8_t *d_out, void *stream);
+
+/* pbvd_decode_host with packed q-bit input (see pbvd_decode_packed): the
+ * copy pipeline moves the packed words host -> device, unpacks each run's
+ * values on the device as soon as its words have arrived, and decodes the
+ * runs as pbvd_decode_host does.  segments >= 0 (direct access is not
+ * offered for packed input). */
+PBVD_API int pbvd_decode_host_packed(pbvd_ctx *ctx, const uint32_t *h_words, int q, size_t n_stages,
+                                     uint8_t *h_out, int segments, void *stream);
 
 /* Number of soft values d_llr must hold for n_stages stages. */
 PBVD_API int pbvd_llr_count(const pbvd_ctx *ctx, size_t n_stages, size_t *count);
@@ -228,16 +296,19 @@ PBVD_API int pbvd_autotune(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages, 
  * pbvd_noalloc_max_survivor_bytes() bytes (16 MiB) that every GPU loading the
  * library holds until exit, and calls no cudaMalloc, cudaFree or other
  * allocating routine.  Arguments and results are those of pbvd_decode; the
- * survivor bits always live in that array (the context's survivors_in_smem
- * setting is ignored).
+ * survivor bits live in shared memory when the context's configuration
+ * places them there (as pbvd_decode would: few blocks, or survivors_in_smem
+ * = 1), otherwise in that array.
  * With an automatic configuration it uses fewer threads per pair of blocks
  * (smaller survivor records) when that is what makes the bits fit.  Returns
  * PBVD_EINVAL when the launch would still need more survivor bytes than the
  * array holds (for the K=7 rate-1/2 code with D=512, L=42: about 1.9 million
  * stages) or when the current device is not the context's.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress), so
- * make it outside stream capture.  All calls share the array: calls whose
- * work overlaps on the GPU (other streams, other host threads) race on it. */
+ * make it outside stream capture; the address is kept until the process
+ * exits, so do not reset the device (cudaDeviceReset) while using the
+ * library.  All calls share the array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it. */
 PBVD_API int pbvd_decode_noalloc(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
                                  uint8_t *d_out, void *stream);
 

@@ -68,6 +68,10 @@ def _load():
             "orc_viterbi_block_metrics": (I, [I, I, P, P, I64, I64, I64, I64, I64, P, P]),
             "orc_viterbi_block_variant": (I, [I, I, P, P, I64, I64, I64, I64, I64, I, P, P]),
             "orc_encode_tailbiting": (I64, [I, I, P, P, I64, P]),
+            "orc_unpack_soft": (I, [I, P, I64, P]),
+            "orc_branch_metric_q": (I64, [I, P, U32, I]),
+            "orc_acs_stage_q": (None, [I, I, P, P, I, P, P, P]),
+            "orc_viterbi_block_q": (I, [I, I, P, P, I64, I64, I64, I, P]),
             "orc_viterbi_window": (I, [I, I, P, P, I64, I64, I64, P]),
             "orc_brute_force": (I, [I, I, P, P, I, P, P, P]),
         }
@@ -266,6 +270,48 @@ def encode_tailbiting(K: int, gens, msg) -> np.ndarray:
     if _load().orc_encode_tailbiting(K, R, _ptr(g), _ptr(m), len(m), _ptr(out)) < 0:
         raise ValueError("tail-biting frames need k >= K - 1")
     return out.reshape(len(m), R)
+
+
+def q_max(q: int) -> int:
+    """Largest magnitude Q of a q-bit soft value (1 for hard decisions)."""
+    return 1 if q == 1 else (1 << (q - 1)) - 1
+
+
+def unpack_soft(q: int, words, count: int) -> np.ndarray:
+    """Sec. IV-C packing: count q-bit soft values from uint32 words."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32))
+    out = np.zeros(max(count, 1), dtype=np.int8)
+    if _load().orc_unpack_soft(q, _ptr(w), count, _ptr(out)) != 0:
+        raise ValueError("q must be 1..8")
+    return out[:count].copy()
+
+
+def branch_metric_q(lam, c: int, Q: int) -> int:
+    l = _i8(lam)
+    return int(_load().orc_branch_metric_q(len(l), _ptr(l), c, Q))
+
+
+def acs_stage_q(K: int, gens, lam, Q: int, pm_prev):
+    g = _gens(gens)
+    l = _i8(lam)
+    N = 1 << (K - 1)
+    pp = np.ascontiguousarray(np.asarray(pm_prev, dtype=np.int64))
+    pn = np.zeros(N, dtype=np.int64)
+    dec = np.zeros(N, dtype=np.uint8)
+    _load().orc_acs_stage_q(K, len(g), _ptr(g), _ptr(l), Q, _ptr(pp), _ptr(pn), _ptr(dec))
+    return pn, dec
+
+
+def viterbi_block_q(K: int, gens, llr_q, D: int, L: int, Q: int) -> np.ndarray:
+    """Block form on unpacked q-bit values (n, R) with mu = +-Q."""
+    g = _gens(gens)
+    R = len(g)
+    l = _i8(llr_q).reshape(-1)
+    n = len(l) // R
+    out = np.zeros(n, dtype=np.uint8)
+    if _load().orc_viterbi_block_q(K, R, _ptr(g), _ptr(l), n, D, L, Q, _ptr(out)) != 0:
+        raise ValueError("orc_viterbi_block_q failed")
+    return out
 
 
 def viterbi_window(K: int, gens, llr, D: int, L: int) -> np.ndarray:

@@ -35,6 +35,10 @@
  *                       of the classic VA (Sec. II) and/or circular windows
  *                       for tail-biting frames (not in the paper);
  *   orc_encode_tailbiting  tail-biting encoder (start state = end state);
+ *   orc_unpack_soft, orc_branch_metric_q, orc_viterbi_block_q
+ *                       Sec. IV-C: q-bit soft values packed floor(32/q) to a
+ *                       32-bit word (q = 1: hard decisions), decoded by the
+ *                       block form with mu = +-Q, Q = 2^{q-1} - 1;
  *   orc_viterbi_window  continuous (carried-metric) form for streaming:
  *                       Eq. (1) run without restarts over an unbounded stream;
  *                       each segment of D stages is released once L further
@@ -410,6 +414,113 @@ int orc_viterbi_block(int K, int R, const uint32_t *gens, const int8_t *llr, int
         return -1;
     int64_t nb = (n + D - 1) / D;
     return orc_viterbi_block_range(K, R, gens, llr, n, D, L, 0, nb, out);
+}
+
+/* ------------------------------------------- q-bit quantised inputs -- */
+
+/* Sec. IV-C: soft values quantised to q bits, floor(32/q) of them packed in
+ * one 32-bit word: value i sits in word i / m (m = floor(32/q)) at bits
+ * [q (i mod m), q (i mod m) + q), as a q-bit two's complement number.  q = 1
+ * is hard decision: the bit is the received code bit, read as +1 (bit 0) or
+ * -1 (bit 1).  Unpacks count values into out.  Returns 0, -1 for bad q. */
+int orc_unpack_soft(int q, const uint32_t *words, int64_t count, int8_t *out)
+{
+    if (q < 1 || q > 8)
+        return -1;
+    int64_t m = 32 / q;
+    for (int64_t i = 0; i < count; i++) {
+        uint32_t w = words[i / m];
+        int shift = (int)(q * (i % m));
+        uint32_t u = (w >> shift) & ((1u << q) - 1u);
+        if (q == 1) {
+            out[i] = u ? -1 : 1;
+        } else {
+            int32_t val = (int32_t)u;
+            if (u & (1u << (q - 1)))
+                val -= (int32_t)(1u << q);
+            out[i] = (int8_t)val;
+        }
+    }
+    return 0;
+}
+
+/* The branch metric of Sec. II on q-bit values: sum_r |lambda_r - mu(c_r)|
+ * with mu(0) = +Q, mu(1) = -Q, Q = 2^{q-1} - 1 the largest magnitude (Q = 1
+ * for hard decisions, where the metric is twice the Hamming distance);
+ * values below -Q read as -Q. */
+int64_t orc_branch_metric_q(int R, const int8_t *lam, uint32_t c, int Q)
+{
+    int64_t bm = 0;
+    for (int r = 0; r < R; r++) {
+        int64_t l = lam[r] < -Q ? -Q : lam[r];
+        int bit = (int)((c >> (R - 1 - r)) & 1u);
+        int64_t mu = bit ? -Q : Q;
+        int64_t diff = l - mu;
+        bm += diff < 0 ? -diff : diff;
+    }
+    return bm;
+}
+
+/* Eq. (1) for one stage with orc_branch_metric_q (tie rule as orc_acs_stage). */
+void orc_acs_stage_q(int K, int R, const uint32_t *gens, const int8_t *lam, int Q,
+                     const int64_t *pm_prev, int64_t *pm_next, uint8_t *dec)
+{
+    int v = K - 1;
+    uint32_t N = 1u << v;
+    for (uint32_t j = 0; j < N; j++) {
+        uint32_t jp = j & ((1u << (v - 1)) - 1u);
+        int x = (int)(j >> (v - 1));
+        uint32_t i0 = 2 * jp, i1 = 2 * jp + 1;
+        int64_t m0 = pm_prev[i0] + orc_branch_metric_q(R, lam, orc_codeword(K, R, gens, i0, x), Q);
+        int64_t m1 = pm_prev[i1] + orc_branch_metric_q(R, lam, orc_codeword(K, R, gens, i1, x), Q);
+        if (m1 < m0) {
+            pm_next[j] = m1;
+            dec[j] = 1;
+        } else {
+            pm_next[j] = m0;
+            dec[j] = 0;
+        }
+    }
+}
+
+/* The block form (Sec. III-A, Algorithm 1) on unpacked q-bit values
+ * (n * R of them, stage major) with the metric of orc_branch_metric_q. */
+int orc_viterbi_block_q(int K, int R, const uint32_t *gens, const int8_t *llr_q, int64_t n,
+                        int64_t D, int64_t L, int Q, uint8_t *out)
+{
+    int v = K - 1;
+    uint32_t N = 1u << v;
+    if (D <= 0 || L < 0 || Q < 1)
+        return -1;
+    if (n <= 0)
+        return 0;
+    int64_t span = D + 2 * L;
+    int64_t nb = (n + D - 1) / D;
+    int64_t *pm = (int64_t *)malloc(sizeof(int64_t) * N);
+    int64_t *pm2 = (int64_t *)malloc(sizeof(int64_t) * N);
+    uint8_t *dec = (uint8_t *)malloc((size_t)span * N);
+    if (!pm || !pm2 || !dec) {
+        free(pm); free(pm2); free(dec);
+        return -1;
+    }
+    for (int64_t b = 0; b < nb; b++) {
+        int64_t f0, f1, o0, o1;
+        orc_block_geometry(n, D, L, b, &f0, &f1, &o0, &o1);
+        for (uint32_t j = 0; j < N; j++)
+            pm[j] = (f0 == 0) ? (j == 0 ? 0 : ORC_BIG) : 0;
+        for (int64_t s = f0; s <= f1; s++) {
+            orc_acs_stage_q(K, R, gens, llr_q + s * R, Q, pm, pm2, dec + (s - f0) * N);
+            int64_t *t = pm; pm = pm2; pm2 = t;
+        }
+        uint32_t state = 0;
+        for (int64_t s = f1; s >= o0; s--) {
+            if (s < o1)
+                out[s] = (uint8_t)orc_state_bit(K, state);
+            state = orc_predecessor(K, state, dec[(s - f0) * N + state]);
+        }
+    }
+    free(pm); free(pm2); free(dec);
+    return 0;
 }
 
 /* ----------------------------------------------- carried-metric stream -- */

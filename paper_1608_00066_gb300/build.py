@@ -48,16 +48,43 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps() + [__file__])
 
 
+# Headers the run-time compiled kernels need (pbvd_jit.cu embeds them).
+JIT_HEADERS = ("pbvd_device.cuh", "pbvd_internal.h", "pbvd_rtc_types.h")
+
+
+def write_jit_sources() -> str:
+    """Writes _build/pbvd_jit_src.inc: the kernel headers as string literals,
+    so that the library compiles kernels for new codes without reading any
+    file at run time."""
+    path = os.path.join(BUILD, "pbvd_jit_src.inc")
+    parts = ["// Generated by build.py from csrc/: the headers of run-time compiled kernels.",
+             "constexpr int kJitNumHeaders = %d;" % len(JIT_HEADERS),
+             "const char* const kJitHeaderNames[] = {%s};" % ", ".join('"%s"' % h for h in JIT_HEADERS),
+             "const char* const kJitHeaders[] = {"]
+    for h in JIT_HEADERS:
+        text = open(os.path.join(CSRC, h)).read()
+        if ")PBVDJIT\"" in text:
+            raise RuntimeError("%s contains the raw-string delimiter" % h)
+        parts.append('R"PBVDJIT(' + text + ')PBVDJIT",')
+    parts.append("};")
+    data = "\n".join(parts) + "\n"
+    if not os.path.exists(path) or open(path).read() != data:
+        with open(path, "w") as f:
+            f.write(data)
+    return path
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if not force and not extra_flags and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    write_jit_sources()
     cc = nvcc()
     srcs = _sources()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + NVCC_FLAGS + ["-I" + BUILD] + list(extra_flags) + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -71,7 +98,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for obj, log in results:
             sys.stderr.write(log)
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results]
+    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results] + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -12,6 +12,7 @@
 
 #include "pbvd.h"
 #include "pbvd_internal.h"
+#include "pbvd_jit.h"
 
 using namespace pbvd;
 
@@ -50,7 +51,11 @@ Registry& registry() {
     n += register_k7_punctured(buf + n, 64 - n);
     n += register_k9(buf + n, 64 - n);
     n += register_small(buf + n, 64 - n);
+    n += register_k7_r3(buf + n, 64 - n);
+    // room for codes compiled at run time, so that entries never move
+    reg.entries.reserve(4096);
     reg.entries.assign(buf, buf + n);
+    reg.smem_set.reserve(2 * 4096);
     reg.smem_set.assign(2 * n, 48 * 1024);
     BatchKernelEntry bb[4];
     const int nb = register_batch(bb, 4);
@@ -64,11 +69,13 @@ Registry& registry() {
 }
 std::mutex g_reg_mu;
 
-int find_entry(int K, int R, const uint32_t* gens, int T, bool punct) {
+// need_var: only entries that honour the traceback / frame variants.
+int find_entry(int K, int R, const uint32_t* gens, int T, bool punct, bool need_var = false) {
   Registry& reg = registry();
   for (size_t i = 0; i < reg.entries.size(); ++i) {
     const KernelEntry& e = reg.entries[i];
     if (e.K != K || e.R != R || e.T != T || e.punct != punct) continue;
+    if (need_var && !e.variants) continue;
     bool same = true;
     for (int r = 0; r < R; ++r) same = same && (e.gens[r] == gens[r]);
     if (same) return (int)i;
@@ -80,6 +87,38 @@ int code_has_any_kernel(int K, int R, const uint32_t* gens, bool punct) {
   for (int T = 1; T <= 32; T *= 2)
     if (find_entry(K, R, gens, T, punct) >= 0) return 1;
   return 0;
+}
+
+// Registers run-time compiled kernels for a code with none built in (once
+// per code and puncturing); returns whether the code now has kernels.
+int ensure_code_kernels(int K, int R, const uint32_t* gens, bool punct) {
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  if (code_has_any_kernel(K, R, gens, punct)) return 1;
+  Registry& reg = registry();
+  KernelEntry buf[8];
+  const int n = jit_register(K, R, gens, punct, buf, 8);
+  if (n <= 0 || reg.entries.size() + n > reg.entries.capacity()) return 0;
+  for (int i = 0; i < n; ++i) {
+    reg.entries.push_back(buf[i]);
+    reg.smem_set.push_back(48 * 1024);
+    reg.smem_set.push_back(48 * 1024);
+  }
+  return 1;
+}
+
+// Launch of one entry's kernel (built in, or compiled at run time).
+int entry_launch(const KernelEntry& e, int smem_surv, const KArgs& a, int grid, int cta, size_t smem,
+                 cudaStream_t s) {
+  if (e.jit >= 0) {
+    const int rc = jit_launch(e.jit, smem_surv ? 1 : 0, a, grid, cta, smem, s);
+    if (rc != PBVD_OK) {
+      std::lock_guard<std::mutex> lk(g_err_mu);
+      std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s", jit_last_error());
+    }
+    return rc;
+  }
+  PBVD_CUDA(e.launch[smem_surv ? 1 : 0](a, grid, cta, smem, s));
+  return PBVD_OK;
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -115,6 +154,13 @@ struct pbvd_ctx {
   size_t hp_out_cap;
   uint32_t* hp_surv;
   size_t hp_surv_cap;
+  uint32_t* hp_words;    // packed q-bit input of pbvd_decode_host_packed
+  size_t hp_words_cap;
+  int8_t* pk_vals;       // unpacked values of pbvd_decode_packed
+  size_t pk_cap;
+  int mode;              // PBVD_MODE_* flags
+  int8_t* tb_ext;        // tail-biting: the frame with L wrapped stages on each side
+  size_t tb_ext_cap;
 };
 
 namespace {
@@ -136,6 +182,7 @@ int states_max_per_thread() { return 64; }
 
 int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p) {
   Registry& reg = registry();
+  const bool var = c->mode != 0;
   p->n_blocks = ceil_div((int64_t)n_stages, c->D);
   p->n_pairs = ceil_div(p->n_blocks, 2);
   int T = c->cfg.threads_per_pair;
@@ -148,11 +195,11 @@ int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p) {
     while (T < want && T < 32) T *= 2;
     T = std::max(T, tmin);
     T = std::min(T, std::min(32, c->N / 2));
-    while (T > tmin && find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) T /= 2;
-    while (T < 32 && find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) T *= 2;
+    while (T > tmin && find_entry(c->K, c->R, c->gens, T, c->P != 0, var) < 0) T /= 2;
+    while (T < 32 && find_entry(c->K, c->R, c->gens, T, c->P != 0, var) < 0) T *= 2;
   }
   p->T = T;
-  p->entry = find_entry(c->K, c->R, c->gens, T, c->P != 0);
+  p->entry = find_entry(c->K, c->R, c->gens, T, c->P != 0, var);
   if (p->entry < 0) return PBVD_EUNSUPPORTED;
   const KernelEntry& e = reg.entries[p->entry];
   // survivor records per pair: D + L, rounded up to whole blocks of 8 (the
@@ -202,7 +249,17 @@ int grant_smem(int entry, bool smem_surv, size_t bytes) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
   const int slot = 2 * entry + (smem_surv ? 1 : 0);
   if ((int)bytes <= reg.smem_set[slot]) return PBVD_OK;
-  PBVD_CUDA(reg.entries[entry].set_max_smem[smem_surv ? 1 : 0]((int)bytes));
+  const KernelEntry& e = reg.entries[entry];
+  if (e.jit >= 0) {
+    const int rc = jit_set_max_smem(e.jit, smem_surv ? 1 : 0, (int)bytes);
+    if (rc != PBVD_OK) {
+      std::lock_guard<std::mutex> lk2(g_err_mu);
+      std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s", jit_last_error());
+      return rc;
+    }
+  } else {
+    PBVD_CUDA(e.set_max_smem[smem_surv ? 1 : 0]((int)bytes));
+  }
   reg.smem_set[slot] = (int)bytes;
   return PBVD_OK;
 }
@@ -231,10 +288,14 @@ void host_pipeline_release(pbvd_ctx* c) {
   if (c->hp_llr) cudaFree(c->hp_llr);
   if (c->hp_out) cudaFree(c->hp_out);
   if (c->hp_surv) cudaFree(c->hp_surv);
+  if (c->hp_words) cudaFree(c->hp_words);
+  if (c->pk_vals) cudaFree(c->pk_vals);
   c->hp_llr = nullptr;
   c->hp_out = nullptr;
   c->hp_surv = nullptr;
-  c->hp_llr_cap = c->hp_out_cap = c->hp_surv_cap = 0;
+  c->hp_words = nullptr;
+  c->pk_vals = nullptr;
+  c->hp_llr_cap = c->hp_out_cap = c->hp_surv_cap = c->hp_words_cap = c->pk_cap = 0;
 }
 
 int host_pipeline_setup(pbvd_ctx* c) {
@@ -358,6 +419,7 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
     if (!it.ctx || !it.d_llr || !it.d_out || it.n_stages == 0 || it.n_stages > ((size_t)1 << 40))
       return PBVD_EINVAL;
     const pbvd_ctx* c = it.ctx;
+    if (c->mode != 0) return PBVD_EUNSUPPORTED;  // the batch kernel decodes the plain scheme
     int slot = -1;
     for (int s = 0; s < kBatchSlots && slot < 0; ++s) {
       if (be.K[s] != c->K || be.R[s] != c->R || be.punct[s] != (c->P != 0)) continue;
@@ -599,7 +661,9 @@ int pbvd_create(pbvd_ctx** out, int K, int R, const uint32_t* gens, const uint8_
       if (!sent) return PBVD_EINVAL;
     }
   }
-  if (!code_has_any_kernel(K, R, gens, puncture != nullptr)) return PBVD_EUNSUPPORTED;
+  if (!code_has_any_kernel(K, R, gens, puncture != nullptr) &&
+      !ensure_code_kernels(K, R, gens, puncture != nullptr))
+    return PBVD_EUNSUPPORTED;
 
   pbvd_ctx* c = new (std::nothrow) pbvd_ctx();
   if (!c) return PBVD_ENOMEM;
@@ -645,6 +709,7 @@ void pbvd_destroy(pbvd_ctx* c) {
   if (c->batch) pbvd_batch_destroy(c->batch);
   if (c->work || c->hp_ready) cudaDeviceSynchronize();
   if (c->work) cudaFree(c->work);
+  if (c->tb_ext) cudaFree(c->tb_ext);
   host_pipeline_release(c);
   delete c;
 }
@@ -692,6 +757,25 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   Plan p;
   int rc = plan_decode(c, n_stages, &p);
   if (rc != PBVD_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int8_t* src = d_llr;
+  size_t src_count = 0;
+  pbvd_llr_count(c, n_stages, &src_count);
+  if (c->mode & PBVD_MODE_TAILBITING) {
+    // the frame with L stages wrapped around on each side: index e holds
+    // stage (e - L) mod n, so every block's window is one contiguous range
+    const size_t n = n_stages, L = (size_t)c->L, R = (size_t)c->R;
+    rc = grow_device(&c->tb_ext, &c->tb_ext_cap, (n + 2 * L) * R);
+    if (rc != PBVD_OK) return rc;
+    for (size_t e = 0; e < n + 2 * L;) {
+      const size_t stg = (e + n * ((L + n - 1) / n + 1) - L) % n;  // (e - L) mod n
+      const size_t len = std::min(n + 2 * L - e, n - stg);
+      PBVD_CUDA(cudaMemcpyAsync(c->tb_ext + e * R, d_llr + stg * R, len * R, cudaMemcpyDeviceToDevice, st));
+      e += len;
+    }
+    src = c->tb_ext;
+    src_count = (n + 2 * L) * R;
+  }
   if (!p.smem_surv) {
     rc = ensure_work(c, p.surv_bytes);
     if (rc != PBVD_OK) return rc;
@@ -700,7 +784,7 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   if (rc != PBVD_OK) return rc;
   KArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.llr = d_llr;
+  a.llr = src;
   a.out = d_out;
   a.surv = static_cast<uint32_t*>(c->work);
   a.n = (int64_t)n_stages;
@@ -716,23 +800,72 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   a.punct_C = c->punct_C;
   std::memcpy(a.punct_off, c->punct_off, sizeof(a.punct_off));
   std::memcpy(a.punct_pre, c->punct_pre, sizeof(a.punct_pre));
-  size_t cnt = 0;
-  pbvd_llr_count(c, n_stages, &cnt);
-  a.llr_count = (int64_t)cnt;
+  a.llr_count = (int64_t)src_count;
+  a.tb_argmin = (c->mode & PBVD_MODE_ARGMIN) ? 1 : 0;
+  a.circular = (c->mode & PBVD_MODE_TAILBITING) ? 1 : 0;
   const int64_t grid = ceil_div(p.n_pairs, p.groups);
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
-  PBVD_CUDA(e.launch[p.smem_surv ? 1 : 0](a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
+  return entry_launch(e, p.smem_surv, a, (int)grid, p.cta, p.smem_bytes, st);
+}
+
+int pbvd_decode_two_kernel(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_out, void* stream) {
+  if (!c || !d_llr || !d_out || n_stages == 0) return PBVD_EINVAL;
+  if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
+  const int nc = two_kernel_groups(c->K, c->R, c->gens);
+  if (nc < 0 || c->P || c->mode) return PBVD_EUNSUPPORTED;
+  const int64_t nb = ceil_div((int64_t)n_stages, c->D);
+  // SP[D + 2L][N_c][N_t] survivor words
+  const size_t sp_bytes = (size_t)(c->D + 2 * c->L) * (size_t)nc * (size_t)nb * 4;
+  int rc = ensure_work(c, sp_bytes);
+  if (rc != PBVD_OK) return rc;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.llr = d_llr;
+  a.out = d_out;
+  a.n = (int64_t)n_stages;
+  a.n_blocks = nb;
+  a.D = c->D;
+  a.L = c->L;
+  size_t cnt = 0;
+  pbvd_llr_count(c, n_stages, &cnt);
+  a.llr_count = (int64_t)cnt;
+  PBVD_CUDA(two_kernel_launch(c->K, a, static_cast<uint32_t*>(c->work), nb, static_cast<cudaStream_t>(stream)));
   return PBVD_OK;
 }
 
-int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t* h_out, int segments,
+int pbvd_set_mode(pbvd_ctx* c, int flags) {
+  if (!c || (flags & ~(PBVD_MODE_ARGMIN | PBVD_MODE_TAILBITING))) return PBVD_EINVAL;
+  if ((flags & PBVD_MODE_TAILBITING) && c->P) return PBVD_EUNSUPPORTED;
+  c->mode = flags;
+  return PBVD_OK;
+}
+
+int pbvd_get_mode(const pbvd_ctx* c, int* flags) {
+  if (!c || !flags) return PBVD_EINVAL;
+  *flags = c->mode;
+  return PBVD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// pbvd_decode_host and pbvd_decode_host_packed: h_in holds int8 soft values
+// (q = 0) or q-bit values packed floor(32/q) to a 32-bit word.
+int decode_host_impl(pbvd_ctx* c, const void* h_in, int q, size_t n_stages, uint8_t* h_out, int segments,
                      void* stream) {
-  if (!c || !h_llr || !h_out || n_stages == 0 || segments < -1) return PBVD_EINVAL;
+  if (!c || !h_in || !h_out || n_stages == 0 || segments < -1) return PBVD_EINVAL;
   if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
+  if (q < 0 || q > 8) return PBVD_EINVAL;
+  const int8_t* h_llr = static_cast<const int8_t*>(h_in);
+  const uint32_t* h_words = static_cast<const uint32_t*>(h_in);
+  const int64_t per_word = q > 0 ? 32 / q : 1;
   int dev = -1;
   PBVD_CUDA(cudaGetDevice(&dev));
   if (dev != c->device) return PBVD_EINVAL;
+  if (segments < 0 && q > 0) return PBVD_EUNSUPPORTED;
+  if (c->mode & PBVD_MODE_TAILBITING) return PBVD_EUNSUPPORTED;
   if (segments < 0) {
     // direct access: the kernel reads the soft values from host memory and
     // writes the bits back over the host link itself, with no staging copy
@@ -780,6 +913,11 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
   if (rc != PBVD_OK) return rc;
   rc = grow_device(&c->hp_surv, &c->hp_surv_cap, (size_t)kHostLanes * slice_words * 4);
   if (rc != PBVD_OK) return rc;
+  const size_t n_words = q > 0 ? (size_t)((llr_bytes + per_word - 1) / per_word) : 0;
+  if (q > 0) {
+    rc = grow_device(&c->hp_words, &c->hp_words_cap, n_words * 4);
+    if (rc != PBVD_OK) return rc;
+  }
   rc = grant_smem(p.entry, false, p.smem_bytes);
   if (rc != PBVD_OK) return rc;
 
@@ -800,8 +938,16 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
     size_t v0 = 0, v1 = 0;
     pbvd_llr_count(c, s0, &v0);
     pbvd_llr_count(c, s1, &v1);
-    if (v1 > v0)
+    if (v1 > v0 && q == 0) {
       PBVD_CUDA(cudaMemcpyAsync(c->hp_llr + v0, h_llr + v0, v1 - v0, cudaMemcpyHostToDevice, c->hp_copy));
+    } else if (v1 > v0) {
+      // the words holding values [v0, v1) (a word shared with the previous
+      // copy is copied again; same bytes, same stream), then their values
+      const size_t w0 = v0 / per_word, w1 = std::min(n_words, (v1 + per_word - 1) / per_word);
+      PBVD_CUDA(cudaMemcpyAsync(c->hp_words + w0, h_words + w0, (w1 - w0) * 4, cudaMemcpyHostToDevice,
+                                c->hp_copy));
+      PBVD_CUDA(launch_unpack(q, c->hp_words, (int64_t)v0, (int64_t)v1, c->hp_llr, c->hp_copy));
+    }
     PBVD_CUDA(cudaEventRecord(c->hp_in[i], c->hp_copy));
   }
   KArgs a;
@@ -819,6 +965,7 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
   std::memcpy(a.punct_off, c->punct_off, sizeof(a.punct_off));
   std::memcpy(a.punct_pre, c->punct_pre, sizeof(a.punct_pre));
   a.llr_count = (int64_t)llr_bytes;
+  a.tb_argmin = (c->mode & PBVD_MODE_ARGMIN) ? 1 : 0;
   for (int i = 0; i < S; ++i) {
     const int l = i % kHostLanes;
     cudaStream_t st = c->hp_lane[l];
@@ -830,7 +977,8 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
     a.surv = c->hp_surv + (size_t)l * slice_words;
     a.surv_pairs = a.n_pairs;
     const int64_t grid = ceil_div(a.n_pairs, p.groups);
-    PBVD_CUDA(e.launch[0](a, (int)grid, p.cta, p.smem_bytes, st));
+    rc = entry_launch(e, 0, a, (int)grid, p.cta, p.smem_bytes, st);
+    if (rc != PBVD_OK) return rc;
     const size_t o0 = (size_t)(r.b0 * c->D / 8);
     const size_t o1 = (std::min(n_stages, (size_t)(r.b1 * c->D)) + 7) / 8;
     PBVD_CUDA(cudaMemcpyAsync(h_out + o0, c->hp_out + o0, o1 - o0, cudaMemcpyDeviceToHost, st));
@@ -840,6 +988,33 @@ int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t*
     PBVD_CUDA(cudaStreamWaitEvent(user, c->hp_done[l], 0));
   }
   return PBVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbvd_decode_host(pbvd_ctx* c, const int8_t* h_llr, size_t n_stages, uint8_t* h_out, int segments,
+                     void* stream) {
+  return decode_host_impl(c, h_llr, 0, n_stages, h_out, segments, stream);
+}
+
+int pbvd_decode_host_packed(pbvd_ctx* c, const uint32_t* h_words, int q, size_t n_stages, uint8_t* h_out,
+                            int segments, void* stream) {
+  if (q < 1 || q > 8 || segments < 0) return PBVD_EINVAL;
+  return decode_host_impl(c, h_words, q, n_stages, h_out, segments, stream);
+}
+
+int pbvd_decode_packed(pbvd_ctx* c, const uint32_t* d_words, int q, size_t n_stages, uint8_t* d_out,
+                       void* stream) {
+  if (!c || !d_words || !d_out || n_stages == 0 || q < 1 || q > 8) return PBVD_EINVAL;
+  if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
+  size_t count = 0;
+  pbvd_llr_count(c, n_stages, &count);
+  int rc = grow_device(&c->pk_vals, &c->pk_cap, count + 16);
+  if (rc != PBVD_OK) return rc;
+  PBVD_CUDA(launch_unpack(q, d_words, 0, (int64_t)count, c->pk_vals, static_cast<cudaStream_t>(stream)));
+  return pbvd_decode(c, c->pk_vals, n_stages, d_out, stream);
 }
 
 int pbvd_decode_batch(const pbvd_batch_item* items, size_t n_items, void* stream) {
@@ -913,7 +1088,9 @@ void pbvd_batch_destroy(pbvd_batch* b) {
 // stand-in), so its device address is looked up once per device with
 // cudaGetSymbolAddress while that device is current, and passed to the
 // kernel.  That lookup happens on the first call on each device, so make the
-// first call outside any stream capture.  All calls share the array and it
+// first call outside any stream capture.  The looked-up address is kept for
+// the life of the process, so the device must not be reset
+// (cudaDeviceReset) while the library is in use.  All calls share the array and it
 // keeps the last call's contents: nothing needs clearing (every survivor word
 // the traceback reads is written earlier in the same launch), but calls whose
 // work overlaps on the GPU race on it.
@@ -952,21 +1129,27 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   int dev = -1;
   PBVD_CUDA(cudaGetDevice(&dev));
   if (dev != c->device) return PBVD_EINVAL;
-  // the survivor bits always live in the fixed array here
+  if (c->mode & PBVD_MODE_TAILBITING) return PBVD_EUNSUPPORTED;  // needs the wrapped copy of the frame
+  // survivor bits in shared memory (when the context's configuration picks
+  // that placement; it allocates nothing) or in the fixed array
   pbvd_ctx cc = *c;
-  cc.cfg.survivors_in_smem = 0;
   Plan p;
   int rc = plan_decode(&cc, n_stages, &p);
   if (rc != PBVD_OK) return rc;
+  if (!p.smem_surv) {
+    cc.cfg.survivors_in_smem = 0;
+    rc = plan_decode(&cc, n_stages, &p);
+    if (rc != PBVD_OK) return rc;
+  }
   // with an automatic thread count, fall back to fewer threads per pair
   // (smaller survivor records) until the survivor bits fit the array
-  while (c->cfg.threads_per_pair == 0 && p.surv_bytes > kNoAllocSurvivorBytes && p.T > 1) {
+  while (!p.smem_surv && c->cfg.threads_per_pair == 0 && p.surv_bytes > kNoAllocSurvivorBytes && p.T > 1) {
     cc.cfg.threads_per_pair = p.T / 2;
     if (find_entry(c->K, c->R, c->gens, cc.cfg.threads_per_pair, c->P != 0) < 0) break;
     rc = plan_decode(&cc, n_stages, &p);
     if (rc != PBVD_OK) return rc;
   }
-  if (p.surv_bytes > kNoAllocSurvivorBytes) return PBVD_EINVAL;
+  if (!p.smem_surv && p.surv_bytes > kNoAllocSurvivorBytes) return PBVD_EINVAL;
   uint32_t* surv = nullptr;
   rc = noalloc_survivors(dev, &surv);
   if (rc != PBVD_OK) return rc;
@@ -984,8 +1167,8 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   a.surv_rs = registry().entries[p.entry].words_per_stage;
   a.D = c->D;
   a.L = c->L;
-  a.smem_surv = 0;
-  a.smem_rec_words = 0;
+  a.smem_surv = p.smem_surv;
+  a.smem_rec_words = p.smem_surv ? p.rec_words : 0;
   a.punct_P = c->P;
   a.punct_C = c->punct_C;
   std::memcpy(a.punct_off, c->punct_off, sizeof(a.punct_off));
@@ -993,11 +1176,11 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   size_t cnt = 0;
   pbvd_llr_count(c, n_stages, &cnt);
   a.llr_count = (int64_t)cnt;
+  a.tb_argmin = (c->mode & PBVD_MODE_ARGMIN) ? 1 : 0;
   const int64_t grid = ceil_div(p.n_pairs, p.groups);
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
-  PBVD_CUDA(e.launch[p.smem_surv ? 1 : 0](a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream)));
-  return PBVD_OK;
+  return entry_launch(e, p.smem_surv, a, (int)grid, p.cta, p.smem_bytes, static_cast<cudaStream_t>(stream));
 }
 
 size_t pbvd_noalloc_max_survivor_bytes(void) { return kNoAllocSurvivorBytes; }
@@ -1110,7 +1293,7 @@ int pbvd_stream_open(pbvd_stream** out, pbvd_ctx* c, size_t max_push, uint8_t* d
   if (!out) return PBVD_EINVAL;
   *out = nullptr;
   if (!c || !d_out || max_push == 0 || max_push > ((size_t)1 << 24) || out_capacity == 0) return PBVD_EINVAL;
-  if (c->P) return PBVD_EUNSUPPORTED;
+  if (c->P || c->mode != 0) return PBVD_EUNSUPPORTED;  // streams: the carried-metric window form only
   const int entry = find_stream_entry(c);
   if (entry < 0) return PBVD_EUNSUPPORTED;
   const StreamKernelEntry& e = registry().stream[entry];

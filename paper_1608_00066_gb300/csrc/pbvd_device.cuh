@@ -40,9 +40,12 @@
 // 16 + (k & 15) for PB B.  The traceback walks directly in psi coordinates.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+#include "pbvd_rtc_types.h"
+#else
 #include <cstdint>
-#include <type_traits>
 #include <cuda_runtime.h>
+#endif
 
 #include "pbvd_internal.h"
 
@@ -54,6 +57,12 @@ constexpr uint32_t kLamMax2 = 0x00FE00FEu;    // 254 in both lanes
 constexpr int kRing = 16;                      // traceback prefetch: stages per chunk
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+// A compile-time int carried by a type (selects a phase in generic lambdas).
+template <int V>
+struct IntC {
+  static constexpr int value = V;
+};
 
 // ------------------------------------------------------------------ code --
 
@@ -203,19 +212,28 @@ __device__ __forceinline__ PbRun pb_run(const KArgs& a, const int8_t* llr, uint8
                                         int64_t b) {
   const int D = a.D, L = a.L;
   const int64_t s = b * D - L, e = (b + 1) * D + L;
-  const int64_t f0 = s < 0 ? 0 : s;
-  const int64_t f1 = (e < n ? e : n) - 1;
+  int64_t f0 = s < 0 ? 0 : s;
+  int64_t f1 = (e < n ? e : n) - 1;
   const int64_t o0 = b * D;
   const int64_t o1 = (b + 1) * D < n ? (b + 1) * D : n;
+  if (a.circular) {
+    // tail-biting frame: the window wraps around the frame, read from a copy
+    // that holds stages [-L, n + L) (stage s at index s + L)
+    f0 = o0 - L;
+    f1 = o1 + L - 1;
+  }
   PbRun r;
   r.delta = (int)(L - (o0 - f0));
   r.len = (int)(f1 - f0 + 1);
   r.iend = r.delta + r.len - 1;
   r.nout = (int)(o1 - o0);
-  r.known_start = (f0 == 0);
+  r.known_start = (f0 == 0) && !a.circular;
   r.dst = out + (o0 >> 3);
   int64_t v0;
-  if (a.punct_P == 0) {
+  if (a.circular) {
+    r.f0mod = 0;
+    v0 = (f0 + L) * R;
+  } else if (a.punct_P == 0) {
     r.f0mod = 0;
     v0 = f0 * R;
   } else {
@@ -438,6 +456,35 @@ __device__ __forceinline__ uint32_t thread_swap(int tau, int ph) {
   return m;
 }
 
+// The state with the smallest metric of PB x (0: low lanes, 1: high lanes)
+// over the group's N states, after a stage of phase ph, when state u sits at
+// physical index psi = rotl_v(u, ph + 1); ties keep the lowest state index
+// (the start state S_E of the classic VA, Sec. II).  Returns its physical
+// index, where the traceback of that stage starts.  All T lanes of the group
+// must call it together.
+template <class C, int T>
+__device__ __forceinline__ int argmin_state(const uint32_t (&pm)[Shape<C, T>::M], int tau, unsigned gmask, int ph,
+                                            int x) {
+  using S = Shape<C, T>;
+  const int rot = (ph + 1) % C::v;
+  uint32_t best = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < S::M; ++k) {
+    const uint32_t m = x ? (pm[k] >> 16) : (pm[k] & 0xffffu);
+    const uint32_t u = rotr_v<C::v>(((uint32_t)tau << S::r) | (uint32_t)k, rot);
+    const uint32_t key = (m << 9) | u;
+    best = key < best ? key : best;
+  }
+  if constexpr (T > 1) {
+#pragma unroll
+    for (int off = 1; off < T; off <<= 1) {
+      const uint32_t o = __shfl_xor_sync(gmask, best, off, T);
+      best = o < best ? o : best;
+    }
+  }
+  return (int)rotl_v<C::v>(best & 0x1ffu, rot);
+}
+
 // ------------------------------------------------------------- the kernel --
 
 template <class C, int T>
@@ -473,11 +520,12 @@ struct PairWork {
 // STORE says whether all of its stages (i >= L) or none of them keep
 // survivor records, so the period is one branch-free basic block.  SMEM:
 // records go to shared memory (ssv), else to the global workspace (gsv).
-template <class C, int T, bool CHECKED, bool PUNCT, bool SMEM, bool STORE>
+template <class C, int T, bool CHECKED, bool PUNCT, bool SMEM, bool STORE, bool CAP = false>
 __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], const uint32_t (&sel)[Shape<C, T>::P][3],
                                                const KArgs& a, const int8_t* bufA, int cbA, const int8_t* bufB,
                                                int cbB, bool hasB, int i0, int I, int L, int tau, PbRun& gA,
-                                               PbRun& gB, uint32_t*& gsv, int64_t rec_stride, uint32_t*& ssv) {
+                                               PbRun& gB, uint32_t*& gsv, int64_t rec_stride, uint32_t*& ssv,
+                                               int* start = nullptr, unsigned gmask = 0u) {
   using S = Shape<C, T>;
   constexpr int W = S::W;
   constexpr int R = C::R;
@@ -533,6 +581,13 @@ __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], c
     if constexpr (S::P > 5) if (ph == 5) acs_stage<C, T, (S::P > 5 ? 5 : 0)>(pm, wd, bm, kt);
     if constexpr (S::P > 6) if (ph == 6) acs_stage<C, T, (S::P > 6 ? 6 : 0)>(pm, wd, bm, kt);
     if constexpr (S::P > 7) if (ph == 7) acs_stage<C, T, (S::P > 7 ? 7 : 0)>(pm, wd, bm, kt);
+    if constexpr (CAP && CHECKED) {
+      // argmin traceback start: the metrics right after each PB's last stage
+      if (a.tb_argmin) {
+        if (i == gA.iend) start[0] = argmin_state<C, T>(pm, tau, gmask, ph, 0);
+        if (hasB && i == gB.iend) start[1] = argmin_state<C, T>(pm, tau, gmask, ph, 1);
+      }
+    }
     if (CHECKED ? (i >= L) : STORE) {
       if constexpr (SMEM) {
 #pragma unroll
@@ -881,12 +936,12 @@ __device__ __forceinline__ void tb_walk4(const KArgs& a, int64_t gslot, const ui
       }
     };
     auto run_block = [&](bool guarded) {
-      if constexpr (P > 5) step(std::integral_constant<int, (P > 5 ? P - 6 : 0) + 5>{}, P - 6, guarded);
-      if constexpr (P > 4) step(std::integral_constant<int, 4>{}, P - 5, guarded);
-      step(std::integral_constant<int, 3>{}, P - 4, guarded);
-      step(std::integral_constant<int, 2>{}, P - 3, guarded);
-      step(std::integral_constant<int, 1>{}, P - 2, guarded);
-      step(std::integral_constant<int, 0>{}, P - 1, guarded);
+      if constexpr (P > 5) step(IntC<(P > 5 ? P - 6 : 0) + 5>{}, P - 6, guarded);
+      if constexpr (P > 4) step(IntC<4>{}, P - 5, guarded);
+      step(IntC<3>{}, P - 4, guarded);
+      step(IntC<2>{}, P - 3, guarded);
+      step(IntC<1>{}, P - 2, guarded);
+      step(IntC<0>{}, P - 1, guarded);
     };
     if (full) run_block(false); else run_block(true);
     // the byte whose lowest record (a multiple of 8) lies in this block
@@ -918,9 +973,12 @@ __device__ __forceinline__ void tb_walk_any(const KArgs& a, int64_t gslot, const
     tb_walk<C, T, SMEM, NCH>(a, gslot, svs, ring, L, hs, lo, emit_top, jend, x, nout, dst, g_at, psi, g);
 }
 
+// start[x]: physical index of the state PB x's traceback starts from at its
+// last forward stage (0 = S_0, whose index is 0 in every layout).
 template <class C, int T, bool SMEM>
 __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, const PbRun& gB, bool hasB, int J,
-                                               int64_t gslot, uint32_t* scratch, const uint32_t* svs) {
+                                               int64_t gslot, uint32_t* scratch, const uint32_t* svs,
+                                               const int (&start)[2]) {
   using TS = TbShape<C, T>;
   const int L = a.L;
   const int lane = threadIdx.x & 31;
@@ -936,7 +994,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     const int x[2] = {0, 1};
     const int nout[2] = {gA.nout, gB.nout};
     uint8_t* const dst[2] = {gA.dst, gB.dst};
-    int psi[2] = {0, 0}, g[2];
+    int psi[2] = {start[0], start[1]}, g[2];
     tb_walk_any<C, T, SMEM, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
   } else {
     // Segments: lane tau walks segment s of the records of one or both PBs.
@@ -956,7 +1014,9 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     const int stop = jtop / seg;    // top non-empty segment
     const bool active = lo <= jtop;
     const int hs = (s == stop) ? jtop : min(jtop, hi + TS::LAMBDA);
-    int psi[2] = {0, 0}, g[2] = {0, 0};
+    // a walk that begins at its PB's last record starts exactly; the others
+    // begin with a guess (the same state), checked below
+    int psi[2] = {start[0], start[1]}, g[2] = {0, 0};
     if (active) {
       if constexpr (BOTH) {
         const int emit_top[2] = {min(hi, gA.nout - 1), min(hi, gB.nout - 1)};
@@ -972,7 +1032,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
         const int x[1] = {xb};
         const int nout[1] = {g0.nout};
         uint8_t* const dst[1] = {g0.dst};
-        int p1[1] = {0}, g1[1] = {0};
+        int p1[1] = {start[xb]}, g1[1] = {0};
         tb_walk_any<C, T, SMEM, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
         psi[0] = p1[0];
         g[0] = g1[0];
@@ -1014,7 +1074,9 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
   }
 }
 
-template <class C, int T, bool PUNCT, bool SMEM>
+// VAR: honour the traceback and frame variants of KArgs (argmin start state,
+// tail-biting windows); the batch kernel decodes the plain scheme only.
+template <class C, int T, bool PUNCT, bool SMEM, bool VAR = false>
 __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, int64_t gslot,
                                             uint32_t* __restrict__ scratch, uint32_t* __restrict__ svs) {
   using S = Shape<C, T>;
@@ -1059,7 +1121,10 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   const int fast_lo = dmax + (dmax > 0 ? 1 : 0);
   const bool fast_ok = wk.hasB && (PUNCT || R != 2 || (((reinterpret_cast<uintptr_t>(wk.A.llr) |
                                                             reinterpret_cast<uintptr_t>(wk.B.llr)) & 1) == 0));
-  const int fast_hi = fast_ok ? min(gA.iend, gB.iend) - (P - 1) : -1;
+  // with the argmin start the period holding a PB's last stage is checked,
+  // so that its metrics can be captured there
+  const int fast_hi = fast_ok ? min(gA.iend, gB.iend) - (P - 1) - ((VAR && a.tb_argmin) ? 1 : 0) : -1;
+  int start[2] = {0, 0};
 
   const int64_t rec_stride = a.surv_pairs * (int64_t)a.surv_rs;  // global: words per record row
   uint32_t* gsv = a.surv + gslot * a.surv_rs + tau * S::W;
@@ -1094,8 +1159,8 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
       forward_period<C, T, false, PUNCT, SMEM, false>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
                                                       gB, gsv, rec_stride, ssv);
     else
-      forward_period<C, T, true, PUNCT, SMEM, true>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau, gA,
-                                                    gB, gsv, rec_stride, ssv);
+      forward_period<C, T, true, PUNCT, SMEM, true, VAR>(pm, sel, a, bufA, cbA, bufB, cbB, wk.hasB, i0, I, L, tau,
+                                                         gA, gB, gsv, rec_stride, ssv, start, gmask);
     if (i0 + P < I) {
       // end of a full period: transpose back to psi = u (T > 1)
       if constexpr (vector_transpose<C, T>()) {
@@ -1148,7 +1213,7 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 
-  traceback_pair<C, T, SMEM>(a, gA, gB, wk.hasB, J, gslot, scratch, svs);
+  traceback_pair<C, T, SMEM>(a, gA, gB, wk.hasB, J, gslot, scratch, svs, start);
 }
 
 // Minimum resident CTAs of 256 threads the compiler is asked to allow: 2 (at
@@ -1183,7 +1248,7 @@ __global__ void __launch_bounds__(256, decode_min_ctas<C, T>()) pbvd_decode_kern
   wk.B = wk.A;
   wk.B.b = wk.A.b + 1;
   wk.hasB = wk.B.b < a.n_blocks;
-  decode_pair<C, T, PUNCT, SMEM>(a, wk, pair, scratch, svs);
+  decode_pair<C, T, PUNCT, SMEM, true>(a, wk, pair, scratch, svs);
 }
 
 }  // namespace pbvd

@@ -34,6 +34,8 @@ KernelEntry make_entry() {
   e.launch[1] = &launch_decode<C, T, PUNCT, true>;
   e.set_max_smem[0] = &set_max_smem<C, T, PUNCT, false>;
   e.set_max_smem[1] = &set_max_smem<C, T, PUNCT, true>;
+  e.jit = -1;
+  e.variants = true;
   return e;
 }
 
@@ -67,6 +69,8 @@ KernelEntry make_warp_entry() {
   e.launch[1] = &launch_warp<C, PUNCT, true>;
   e.set_max_smem[0] = &set_max_smem_warp<C, PUNCT, false>;
   e.set_max_smem[1] = &set_max_smem_warp<C, PUNCT, true>;
+  e.jit = -1;
+  e.variants = false;
   return e;
 }
 

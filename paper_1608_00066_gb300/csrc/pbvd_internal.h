@@ -1,9 +1,13 @@
 // Internal declarations shared by the host API and the kernel instances.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+#include "pbvd_rtc_types.h"
+#else
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 namespace pbvd {
 
@@ -25,6 +29,8 @@ struct KArgs {
   int32_t punct_P;        // 0: not punctured, else pattern period
   int32_t punct_C;        // values sent per period
   int64_t llr_count;      // soft values readable at llr
+  int32_t tb_argmin;      // 1: each block's traceback starts from its cheapest state (not S_0)
+  int32_t circular;       // 1: tail-biting frame; llr holds stages [-L, n + L) wrapped around
   int16_t punct_off[32 * 4];  // [col][r]: offset in the period, -1 = punctured
   int16_t punct_pre[33];      // values sent in the columns before col
 };
@@ -58,6 +64,7 @@ struct BatchArgs {
   int32_t* counter;         // next tile to take (zeroed before the launch)
 };
 
+#ifndef __CUDACC_RTC__
 using LaunchFn = cudaError_t (*)(const KArgs& a, int grid, int cta, size_t smem, cudaStream_t s);
 using SmemFn = int (*)(int cta_threads, int smem_rec_words);  // dynamic smem bytes of a launch
 using AttrFn = cudaError_t (*)(int smem_bytes);
@@ -72,7 +79,11 @@ struct KernelEntry {
   int scratch_words;       // shared-memory words per group besides records
   LaunchFn launch[2];      // [0]: records in the global workspace, [1]: in shared memory
   AttrFn set_max_smem[2];
+  int jit;                 // -1: compiled into the library; else a kernel compiled at run time
+  bool variants;           // honours KArgs::tb_argmin and KArgs::circular
 };
+
+#endif  // __CUDACC_RTC__
 
 // One stream's push, as the stream kernel sees it.  The stages of the push
 // are the ncarry stages held back from the previous push (carry buffer)
@@ -99,6 +110,7 @@ struct StreamLaunch {
   StreamDev d[kStreamsPerLaunch];
 };
 
+#ifndef __CUDACC_RTC__
 using StreamLaunchFn = cudaError_t (*)(const StreamLaunch& p, cudaStream_t s);
 
 struct StreamKernelEntry {
@@ -123,12 +135,24 @@ struct BatchKernelEntry {
   BatchOccFn occupancy;
 };
 
+// Unpacks q-bit soft values [v0, v1) of words into out[v0 .. v1) as int8,
+// scaled to the decoder's range (pbvd_packed.cu).
+cudaError_t launch_unpack(int q, const uint32_t* words, int64_t v0, int64_t v1, int8_t* out, cudaStream_t s);
+
+// The paper's two-kernel design (pbvd_twokernel.cu): groups N_c of the code
+// (-1 when the ablation is not built for it) and the launch of K1 and K2.
+int two_kernel_groups(int K, int R, const uint32_t* gens);
+cudaError_t two_kernel_launch(int K, const KArgs& a, uint32_t* sp, int64_t sp_pbs, cudaStream_t s);
+
 // Registries filled by the instance files.
 int register_k7(KernelEntry* out, int cap);
 int register_k7_punctured(KernelEntry* out, int cap);
 int register_k9(KernelEntry* out, int cap);
 int register_small(KernelEntry* out, int cap);
+int register_k7_r3(KernelEntry* out, int cap);
 int register_batch(BatchKernelEntry* out, int cap);
 int register_stream(StreamKernelEntry* out, int cap);
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace pbvd

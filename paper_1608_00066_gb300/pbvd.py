@@ -36,7 +36,12 @@ EXPORTS = (
     "pbvd_batch_prepare", "pbvd_batch_run", "pbvd_batch_destroy", "pbvd_autotune",
     "pbvd_stream_open", "pbvd_stream_push", "pbvd_stream_push_many", "pbvd_stream_close",
     "pbvd_stream_released", "pbvd_stream_destroy", "pbvd_batch_update", "pbvd_decode_host",
+    "pbvd_decode_packed", "pbvd_decode_host_packed", "pbvd_set_mode", "pbvd_get_mode",
+    "pbvd_decode_two_kernel",
 )
+
+PBVD_MODE_ARGMIN = 1
+PBVD_MODE_TAILBITING = 2
 
 
 class PbvdError(RuntimeError):
@@ -87,6 +92,16 @@ def load(path: Optional[str] = None):
         lib.pbvd_decode.restype = I
         lib.pbvd_decode_host.argtypes = [V, V, SZ, V, I, V]
         lib.pbvd_decode_host.restype = I
+        lib.pbvd_decode_two_kernel.argtypes = [V, V, SZ, V, V]
+        lib.pbvd_decode_two_kernel.restype = I
+        lib.pbvd_set_mode.argtypes = [V, I]
+        lib.pbvd_set_mode.restype = I
+        lib.pbvd_get_mode.argtypes = [V, ctypes.POINTER(I)]
+        lib.pbvd_get_mode.restype = I
+        lib.pbvd_decode_packed.argtypes = [V, V, I, SZ, V, V]
+        lib.pbvd_decode_packed.restype = I
+        lib.pbvd_decode_host_packed.argtypes = [V, V, I, SZ, V, I, V]
+        lib.pbvd_decode_host_packed.restype = I
         lib.pbvd_llr_count.argtypes = [V, SZ, ctypes.POINTER(SZ)]
         lib.pbvd_llr_count.restype = I
         lib.pbvd_decode_batch.argtypes = [V, SZ, V]
@@ -170,6 +185,36 @@ def pbvd_decode_host(ctx: int, h_llr: int, n_stages: int, h_out: int, segments: 
     an automatic number of runs of blocks, > 0 = that many runs, -1 = direct
     access by the kernel (both buffers mapped page-locked memory)."""
     _check(load().pbvd_decode_host(ctx, h_llr, n_stages, h_out, segments, stream), "pbvd_decode_host")
+
+
+def pbvd_decode_two_kernel(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0) -> None:
+    """The paper's two-kernel design (K1 forward, K2 traceback) as an ablation;
+    the same bits as pbvd_decode."""
+    _check(load().pbvd_decode_two_kernel(ctx, d_llr, n_stages, d_out, stream or None), "pbvd_decode_two_kernel")
+
+
+def pbvd_set_mode(ctx: int, flags: int) -> None:
+    """Decoding variants: PBVD_MODE_ARGMIN | PBVD_MODE_TAILBITING (0 = plain)."""
+    _check(load().pbvd_set_mode(ctx, flags), "pbvd_set_mode")
+
+
+def pbvd_get_mode(ctx: int) -> int:
+    f = ctypes.c_int()
+    _check(load().pbvd_get_mode(ctx, ctypes.byref(f)), "pbvd_get_mode")
+    return int(f.value)
+
+
+def pbvd_decode_packed(ctx: int, d_words: int, q: int, n_stages: int, d_out: int, stream: int = 0) -> None:
+    """Decode of q-bit soft values packed floor(32/q) to a 32-bit word
+    (device pointers; q = 1 is hard decision)."""
+    _check(load().pbvd_decode_packed(ctx, d_words, q, n_stages, d_out, stream or None), "pbvd_decode_packed")
+
+
+def pbvd_decode_host_packed(ctx: int, h_words: int, q: int, n_stages: int, h_out: int, segments: int = 0,
+                            stream: int = 0) -> None:
+    """pbvd_decode_host with packed q-bit input (host pointers)."""
+    _check(load().pbvd_decode_host_packed(ctx, h_words, q, n_stages, h_out, segments, stream or None),
+           "pbvd_decode_host_packed")
 
 
 def pbvd_decode_noalloc(ctx: int, d_llr: int, n_stages: int, d_out: int, stream: int = 0) -> None:
@@ -369,6 +414,34 @@ class Decoder:
             raise ValueError("out must be a contiguous uint8 CPU tensor of %d bytes" % nbytes)
         s = stream if stream is not None else torch.cuda.current_stream()
         pbvd_decode_host(self.ctx, llr.data_ptr(), n_stages, out.data_ptr(), segments, s.cuda_stream)
+        return out
+
+
+    def set_mode(self, argmin: bool = False, tailbiting: bool = False):
+        pbvd_set_mode(self.ctx, (PBVD_MODE_ARGMIN if argmin else 0) | (PBVD_MODE_TAILBITING if tailbiting else 0))
+
+    def decode_packed(self, words, q: int, n_stages: int, out=None, stream=None):
+        """words: int32 tensor of packed q-bit soft values, on the GPU (device
+        decode) or in CPU memory (host pipeline, result in CPU memory)."""
+        import torch
+        if words.dtype not in (torch.int32, torch.uint32) or not words.is_contiguous():
+            raise ValueError("words must be a contiguous 32-bit tensor")
+        m = 32 // q
+        need = (self.llr_count(n_stages) + m - 1) // m
+        if words.numel() < need:
+            raise ValueError("words holds %d words, %d needed" % (words.numel(), need))
+        nbytes = (n_stages + 7) // 8
+        if out is None:
+            out = (torch.empty(nbytes, dtype=torch.uint8, device=words.device) if words.is_cuda
+                   else torch.empty(nbytes, dtype=torch.uint8).pin_memory())
+        if out.numel() < nbytes or out.dtype != torch.uint8 or out.is_cuda != words.is_cuda:
+            raise ValueError("out must be a uint8 tensor of %d bytes beside words" % nbytes)
+        if words.is_cuda:
+            s = stream if stream is not None else torch.cuda.current_stream(words.device)
+            pbvd_decode_packed(self.ctx, words.data_ptr(), q, n_stages, out.data_ptr(), s.cuda_stream)
+        else:
+            s = stream if stream is not None else torch.cuda.current_stream()
+            pbvd_decode_host_packed(self.ctx, words.data_ptr(), q, n_stages, out.data_ptr(), 0, s.cuda_stream)
         return out
 
 

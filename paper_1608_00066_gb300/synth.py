@@ -136,6 +136,56 @@ def bpsk_awgn_int8(rng: np.random.Generator, bits: np.ndarray, ebn0_db: float,
     return np.clip(np.rint(LLR_SCALE * y), -127, 127).astype(np.int8)
 
 
+def quantise_q(y: np.ndarray, q: int) -> np.ndarray:
+    """q-bit soft values of channel outputs y (Sec. IV-C): for q >= 2,
+    clamp(rint(2^(q-2) y), -Q, Q) with Q = 2^(q-1) - 1 (steps of 1/2^(q-2)
+    of the BPSK amplitude); for q = 1 (hard decision) -1 where y < 0, else +1."""
+    if q == 1:
+        return np.where(y < 0, -1, 1).astype(np.int8)
+    Q = (1 << (q - 1)) - 1
+    return np.clip(np.rint(float(1 << (q - 2)) * y), -Q, Q).astype(np.int8)
+
+
+def pack_q(values: np.ndarray, q: int) -> np.ndarray:
+    """Packs q-bit values floor(32/q) to a uint32 word (Sec. IV-C): value i
+    at bits [q (i mod m), q (i mod m) + q) of word i // m, two's complement;
+    for q = 1 the bit is 1 for a negative value (code bit 1)."""
+    v = np.asarray(values, dtype=np.int64)
+    m = 32 // q
+    if q == 1:
+        codes = (v < 0).astype(np.uint64)
+    else:
+        codes = (v & ((1 << q) - 1)).astype(np.uint64)
+    nw = (len(v) + m - 1) // m
+    padded = np.zeros(nw * m, dtype=np.uint64)
+    padded[:len(v)] = codes
+    shifts = (np.arange(m, dtype=np.uint64) * np.uint64(q))
+    words = (padded.reshape(nw, m) << shifts).sum(axis=1, dtype=np.uint64)
+    return words.astype(np.uint32)
+
+
+@dataclass
+class PackedFrame:
+    spec: CodeSpec
+    msg: np.ndarray         # uint8[k]
+    q: int                  # bits per soft value (1 = hard decision)
+    values: np.ndarray      # int8 q-bit soft values, stage major (n * R)
+    words: np.ndarray       # uint32, floor(32/q) values per word
+    n_stages: int
+
+
+def make_packed_frame(spec: CodeSpec, k: int, ebn0_db: float, q: int, seed) -> PackedFrame:
+    """A terminated frame quantised to q bits per sent soft value and packed
+    (punctured codes: the sent values only)."""
+    rng = np.random.default_rng(seed)
+    msg = rng.integers(0, 2, size=k, dtype=np.uint8)
+    bits = puncture_bits(spec, conv_encode(spec, msg))
+    s = 1.0 - 2.0 * bits.astype(np.float64)
+    y = s + noise_sigma(ebn0_db, spec.rate) * rng.standard_normal(len(bits))
+    vals = quantise_q(y, q)
+    return PackedFrame(spec, msg, q, vals, pack_q(vals, q), k + spec.v)
+
+
 def noiseless_int8(bits: np.ndarray) -> np.ndarray:
     """Error-free soft values: +127 for 0, -127 for 1."""
     return (127 - 254 * bits.astype(np.int16)).astype(np.int8)

@@ -36,3 +36,48 @@ def gpu_bits(dec, llr, n, **cfg):
 
 def oracle_bits(spec, frame_llr, n, D, L, blocks=None):
     return oracle.viterbi_block(spec.K, spec.gens, mother_llr(spec, frame_llr, n), D, L, blocks)
+
+
+def _oracle_range(args):
+    """Child process: blocks [b0, b1) of a stream saved as an (n, R) .npy."""
+    path, K, gens, D, L, b0, b1 = args
+    llr = np.load(path, mmap_mode="r")
+    n = llr.shape[0]
+    out = oracle.viterbi_block(K, gens, np.ascontiguousarray(llr), D, L, blocks=(b0, b1))
+    return b0, out[b0 * D:min(b1 * D, n)].copy()
+
+
+def oracle_bits_parallel(spec, frame_llr, n, D, L, procs=None):
+    """Every block of the stream with the CPU oracle, the blocks spread over
+    the host cores (spawned processes, so no forked copy of a CUDA context)."""
+    import multiprocessing as mp
+    import os
+    import tempfile
+    mother = np.ascontiguousarray(mother_llr(spec, frame_llr, n))
+    nb = (n + D - 1) // D
+    procs = procs or os.cpu_count() or 1
+    chunk = max(1, (nb + 4 * procs - 1) // (4 * procs))
+    tmp = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
+    tmp.close()
+    try:
+        np.save(tmp.name, mother)
+        jobs = [(tmp.name, spec.K, tuple(spec.gens), D, L, b, min(nb, b + chunk)) for b in range(0, nb, chunk)]
+        out = np.zeros(n, dtype=np.uint8)
+        with mp.get_context("spawn").Pool(procs) as pool:
+            for b0, bits in pool.imap_unordered(_oracle_range, jobs):
+                out[b0 * D:b0 * D + len(bits)] = bits
+        return out
+    finally:
+        os.unlink(tmp.name)
+
+
+def batch_oracle_job(args):
+    """Child process: oracle bits of frames [f_lo, f_hi) of the mixed-code
+    batch drawn with the given seed, each at its code's (D, L)."""
+    f_lo, f_hi, seed, geometry = args
+    out = []
+    for i in range(f_lo, f_hi):
+        f = synth.batch_frame(i, seed)
+        D, L = geometry[f.spec.name]
+        out.append((i, oracle_bits(f.spec, f.llr, f.n_stages, D, L)))
+    return out

@@ -51,17 +51,74 @@ def test_noalloc_punctured_and_k9():
         dec.close()
 
 
+def _records_per_pair(D, L):
+    """Survivor records per pair of blocks: D + L stages rounded up to whole
+    blocks of eight (the size the library reserves)."""
+    return (D + L + 7) // 8 * 8
+
+
 def test_noalloc_rejects_sizes_beyond_the_array():
     spec = synth.K7_R12
     dec = pbvd.Decoder(spec.K, spec.gens, None, 512, 42)
     dec.set_config(threads_per_pair=2, cta_threads=64, survivors_in_smem=0)
     cap = pbvd.pbvd_noalloc_max_survivor_bytes()
     assert cap == 16 << 20
-    # 554 records of 16 bytes per pair of blocks at T = 2
-    n = (cap // (554 * 16) + 64) * 1024
-    d = torch.zeros(n * 2, dtype=torch.int8, device="cuda")
-    out = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
+    # at T = 2 a record is 16 bytes, 560 records per pair of 512-stage blocks
+    per_pair = _records_per_pair(512, 42) * 16
+    pairs = cap // per_pair
+    n_ok = pairs * 1024              # the largest whole number of pairs that fits
+    n_bad = n_ok + 1                 # one more block, one more pair
+    d = torch.zeros(n_bad * 2, dtype=torch.int8, device="cuda")
+    out = torch.zeros((n_bad + 7) // 8, dtype=torch.uint8, device="cuda")
+    pbvd.pbvd_decode_noalloc(dec.ctx, d.data_ptr(), n_ok, out.data_ptr(), 0)
+    torch.cuda.synchronize()
     with pytest.raises(pbvd.PbvdError) as ei:
-        pbvd.pbvd_decode_noalloc(dec.ctx, d.data_ptr(), n, out.data_ptr(), 0)
+        pbvd.pbvd_decode_noalloc(dec.ctx, d.data_ptr(), n_bad, out.data_ptr(), 0)
     assert ei.value.code == pbvd.PBVD_EINVAL
+    dec.close()
+
+
+def test_noalloc_accepts_a_stream_just_under_the_limit():
+    """The largest stream that fits at T = 2 decodes to pbvd_decode's bits."""
+    spec = synth.K7_R12
+    dec = pbvd.Decoder(spec.K, spec.gens, None, 512, 42)
+    dec.set_config(threads_per_pair=2, cta_threads=64, survivors_in_smem=0)
+    pairs = pbvd.pbvd_noalloc_max_survivor_bytes() // (_records_per_pair(512, 42) * 16)
+    n = pairs * 1024
+    f = synth.make_frame(spec, n - spec.v, 2.0, seed=75)
+    want = _decode(pbvd.pbvd_decode, dec, f.llr, f.n_stages)
+    for _ in range(2):
+        assert np.array_equal(_decode(pbvd.pbvd_decode_noalloc, dec, f.llr, f.n_stages), want)
+    dec.close()
+
+
+def test_noalloc_falls_back_to_fewer_threads_per_pair():
+    """K=7, D=64, L=42: for 2,432 pairs of blocks the automatic configuration
+    uses 16 threads per pair (16-word records: 17.4 MB of survivor bits, more
+    than the array holds); the entry point falls back to 8 threads per pair
+    (8-word records, 8.7 MB) and must still give pbvd_decode's bits."""
+    spec = synth.K7_R12
+    D, L = 64, 42
+    n = 2432 * 2 * D
+    dec = pbvd.Decoder(spec.K, spec.gens, None, D, L)
+    cfg = dec.get_config(n)
+    assert cfg["threads_per_pair"] == 16 and cfg["survivors_in_smem"] == 0
+    assert _records_per_pair(D, L) * 2432 * 16 * 4 > pbvd.pbvd_noalloc_max_survivor_bytes()
+    f = synth.make_frame(spec, n - spec.v, 1.0, seed=76)
+    want = _decode(pbvd.pbvd_decode, dec, f.llr, f.n_stages)
+    for _ in range(2):
+        assert np.array_equal(_decode(pbvd.pbvd_decode_noalloc, dec, f.llr, f.n_stages), want)
+    dec.close()
+
+
+def test_noalloc_keeps_shared_memory_survivors_for_short_frames():
+    """One 4096-bit frame: the automatic configuration keeps the survivors in
+    shared memory, which needs no allocation either."""
+    spec = synth.K7_R12
+    dec = pbvd.Decoder(spec.K, spec.gens, None, 512, 42)
+    f = synth.make_frame(spec, 4096, 3.0, seed=1001)
+    assert dec.get_config(f.n_stages)["survivors_in_smem"] == 1
+    want = _decode(pbvd.pbvd_decode, dec, f.llr, f.n_stages)
+    for _ in range(2):
+        assert np.array_equal(_decode(pbvd.pbvd_decode_noalloc, dec, f.llr, f.n_stages), want)
     dec.close()
