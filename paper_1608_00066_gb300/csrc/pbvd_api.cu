@@ -69,13 +69,14 @@ Registry& registry() {
 }
 std::mutex g_reg_mu;
 
-// need_var: only entries that honour the traceback / frame variants.
-int find_entry(int K, int R, const uint32_t* gens, int T, bool punct, bool need_var = false) {
+// var: the instances that honour the traceback / frame variants (selected
+// by pbvd_set_mode), else the plain ones.
+int find_entry(int K, int R, const uint32_t* gens, int T, bool punct, bool var = false) {
   Registry& reg = registry();
   for (size_t i = 0; i < reg.entries.size(); ++i) {
     const KernelEntry& e = reg.entries[i];
     if (e.K != K || e.R != R || e.T != T || e.punct != punct) continue;
-    if (need_var && !e.variants) continue;
+    if (e.variants != var) continue;
     bool same = true;
     for (int r = 0; r < R; ++r) same = same && (e.gens[r] == gens[r]);
     if (same) return (int)i;
@@ -83,20 +84,21 @@ int find_entry(int K, int R, const uint32_t* gens, int T, bool punct, bool need_
   return -1;
 }
 
-int code_has_any_kernel(int K, int R, const uint32_t* gens, bool punct) {
+int code_has_any_kernel(int K, int R, const uint32_t* gens, bool punct, bool var = false) {
   for (int T = 1; T <= 32; T *= 2)
-    if (find_entry(K, R, gens, T, punct) >= 0) return 1;
+    if (find_entry(K, R, gens, T, punct, var) >= 0) return 1;
   return 0;
 }
 
-// Registers run-time compiled kernels for a code with none built in (once
-// per code and puncturing); returns whether the code now has kernels.
-int ensure_code_kernels(int K, int R, const uint32_t* gens, bool punct) {
+// Registers run-time compiled kernels for a code and puncturing with none of
+// the kind asked for (plain or variant instances); returns whether the code
+// now has such kernels.
+int ensure_code_kernels(int K, int R, const uint32_t* gens, bool punct, bool var = false) {
   std::lock_guard<std::mutex> lk(g_reg_mu);
-  if (code_has_any_kernel(K, R, gens, punct)) return 1;
+  if (code_has_any_kernel(K, R, gens, punct, var)) return 1;
   Registry& reg = registry();
   KernelEntry buf[8];
-  const int n = jit_register(K, R, gens, punct, buf, 8);
+  const int n = jit_register(K, R, gens, punct, var, buf, 8);
   if (n <= 0 || reg.entries.size() + n > reg.entries.capacity()) return 0;
   for (int i = 0; i < n; ++i) {
     reg.entries.push_back(buf[i]);
@@ -732,7 +734,8 @@ int pbvd_set_config(pbvd_ctx* c, const pbvd_config* cfg) {
   if (cfg->threads_per_pair != 0) {
     int T = cfg->threads_per_pair;
     if (T < 1 || T > 32 || (T & (T - 1))) return PBVD_EINVAL;
-    if (find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) return PBVD_EUNSUPPORTED;
+    if (find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0 && find_entry(c->K, c->R, c->gens, T, c->P != 0, true) < 0)
+      return PBVD_EUNSUPPORTED;
   }
   if (cfg->cta_threads != 0 && (cfg->cta_threads < 1 || cfg->cta_threads > 256)) return PBVD_EINVAL;
   if (cfg->survivors_in_smem < -1 || cfg->survivors_in_smem > 1) return PBVD_EINVAL;
@@ -837,6 +840,8 @@ int pbvd_decode_two_kernel(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, ui
 int pbvd_set_mode(pbvd_ctx* c, int flags) {
   if (!c || (flags & ~(PBVD_MODE_ARGMIN | PBVD_MODE_TAILBITING))) return PBVD_EINVAL;
   if ((flags & PBVD_MODE_TAILBITING) && c->P) return PBVD_EUNSUPPORTED;
+  // the variant instances are compiled at run time (on their first launch)
+  if (flags && !ensure_code_kernels(c->K, c->R, c->gens, c->P != 0, true)) return PBVD_EUNSUPPORTED;
   c->mode = flags;
   return PBVD_OK;
 }
@@ -1145,7 +1150,7 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
   // (smaller survivor records) until the survivor bits fit the array
   while (!p.smem_surv && c->cfg.threads_per_pair == 0 && p.surv_bytes > kNoAllocSurvivorBytes && p.T > 1) {
     cc.cfg.threads_per_pair = p.T / 2;
-    if (find_entry(c->K, c->R, c->gens, cc.cfg.threads_per_pair, c->P != 0) < 0) break;
+    if (find_entry(c->K, c->R, c->gens, cc.cfg.threads_per_pair, c->P != 0, c->mode != 0) < 0) break;
     rc = plan_decode(&cc, n_stages, &p);
     if (rc != PBVD_OK) return rc;
   }
@@ -1208,7 +1213,7 @@ int pbvd_autotune(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_
   float best_t = -1.0f;
   int rc = PBVD_OK;
   for (int T = 1; T <= 32 && rc == PBVD_OK; T *= 2) {
-    if (find_entry(c->K, c->R, c->gens, T, c->P != 0) < 0) continue;
+    if (find_entry(c->K, c->R, c->gens, T, c->P != 0, c->mode != 0) < 0) continue;
     for (int cta : {32, 64, 128, 256}) {
       if (cta % T) continue;
       for (int smem = 0; smem <= 1; ++smem) {

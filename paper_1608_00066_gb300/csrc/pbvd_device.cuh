@@ -207,7 +207,8 @@ struct PbRun {
 
 // Geometry of PB b (Sec. III-A): decodes [bD, min((b+1)D, n)) from the
 // forward range [max(0, bD - L), min(n, (b+1)D + L) - 1].
-template <int R>
+// CIRC: the instance may meet tail-biting frames (KArgs::circular).
+template <int R, bool CIRC = false>
 __device__ __forceinline__ PbRun pb_run(const KArgs& a, const int8_t* llr, uint8_t* out, int64_t n,
                                         int64_t b) {
   const int D = a.D, L = a.L;
@@ -216,7 +217,8 @@ __device__ __forceinline__ PbRun pb_run(const KArgs& a, const int8_t* llr, uint8
   int64_t f1 = (e < n ? e : n) - 1;
   const int64_t o0 = b * D;
   const int64_t o1 = (b + 1) * D < n ? (b + 1) * D : n;
-  if (a.circular) {
+  const bool circ = CIRC && a.circular;
+  if (circ) {
     // tail-biting frame: the window wraps around the frame, read from a copy
     // that holds stages [-L, n + L) (stage s at index s + L)
     f0 = o0 - L;
@@ -227,10 +229,10 @@ __device__ __forceinline__ PbRun pb_run(const KArgs& a, const int8_t* llr, uint8
   r.len = (int)(f1 - f0 + 1);
   r.iend = r.delta + r.len - 1;
   r.nout = (int)(o1 - o0);
-  r.known_start = (f0 == 0) && !a.circular;
+  r.known_start = (f0 == 0) && !circ;
   r.dst = out + (o0 >> 3);
   int64_t v0;
-  if (a.circular) {
+  if (circ) {
     r.f0mod = 0;
     v0 = (f0 + L) * R;
   } else if (a.punct_P == 0) {
@@ -1032,7 +1034,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
         const int x[1] = {xb};
         const int nout[1] = {g0.nout};
         uint8_t* const dst[1] = {g0.dst};
-        int p1[1] = {start[xb]}, g1[1] = {0};
+        int p1[1] = {xb ? start[1] : start[0]}, g1[1] = {0};
         tb_walk_any<C, T, SMEM, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
         psi[0] = p1[0];
         g[0] = g1[0];
@@ -1087,8 +1089,8 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   const unsigned gmask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(T - 1)));
   const int L = a.L;
 
-  PbRun gA = pb_run<R>(a, wk.A.llr, wk.A.out, wk.A.n, wk.A.b);
-  PbRun gB = wk.hasB ? pb_run<R>(a, wk.B.llr, wk.B.out, wk.B.n, wk.B.b) : gA;
+  PbRun gA = pb_run<R, VAR>(a, wk.A.llr, wk.A.out, wk.A.n, wk.A.b);
+  PbRun gB = wk.hasB ? pb_run<R, VAR>(a, wk.B.llr, wk.B.out, wk.B.n, wk.B.b) : gA;
   if (!wk.hasB) gB.iend = -1;
   const int I = max(gA.iend, gB.iend) + 1;  // lock-step stages
   const int J = I - L;                      // survivor records (stages L..I-1)
@@ -1229,7 +1231,9 @@ __host__ __device__ constexpr int decode_min_ctas() {
 // Plain launch: pair p of blocks [b_first, n_blocks) of one stream.  SMEM:
 // survivor records of each group in shared memory (a.smem_rec_words words
 // per group), else in a.surv.
-template <class C, int T, bool PUNCT, bool SMEM>
+// VAR: the instance honours the variants of KArgs (argmin traceback start,
+// tail-biting windows); the plain instances carry none of that code.
+template <class C, int T, bool PUNCT, bool SMEM, bool VAR = false>
 __global__ void __launch_bounds__(256, decode_min_ctas<C, T>()) pbvd_decode_kernel(const KArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int groups_per_cta = blockDim.x / T;
@@ -1248,7 +1252,7 @@ __global__ void __launch_bounds__(256, decode_min_ctas<C, T>()) pbvd_decode_kern
   wk.B = wk.A;
   wk.B.b = wk.A.b + 1;
   wk.hasB = wk.B.b < a.n_blocks;
-  decode_pair<C, T, PUNCT, SMEM, true>(a, wk, pair, scratch, svs);
+  decode_pair<C, T, PUNCT, SMEM, VAR>(a, wk, pair, scratch, svs);
 }
 
 }  // namespace pbvd

@@ -35,7 +35,7 @@ KernelEntry make_entry() {
   e.set_max_smem[0] = &set_max_smem<C, T, PUNCT, false>;
   e.set_max_smem[1] = &set_max_smem<C, T, PUNCT, true>;
   e.jit = -1;
-  e.variants = true;
+  e.variants = false;
   return e;
 }
 

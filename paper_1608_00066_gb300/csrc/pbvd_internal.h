@@ -80,7 +80,7 @@ struct KernelEntry {
   LaunchFn launch[2];      // [0]: records in the global workspace, [1]: in shared memory
   AttrFn set_max_smem[2];
   int jit;                 // -1: compiled into the library; else a kernel compiled at run time
-  bool variants;           // honours KArgs::tb_argmin and KArgs::circular
+  bool variants;           // the instance honouring KArgs::tb_argmin and KArgs::circular
 };
 
 #endif  // __CUDACC_RTC__

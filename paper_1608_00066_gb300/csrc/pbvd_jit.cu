@@ -13,6 +13,11 @@
 // as for the built-in codes, so a code chosen at run time decodes at the speed
 // and with the bits of a built-in one.
 //
+// The decoding variants (argmin traceback start, tail-biting frames) are
+// compiled the same way for every code, built-in ones included, when a
+// context first selects them, so that the built-in plain kernels carry none
+// of their code.
+//
 // libnvrtc is opened with dlopen when the first such code is created; without
 // it pbvd_create keeps returning PBVD_EUNSUPPORTED for those codes.  The kernel
 // sources are embedded in the library at build time (pbvd_jit_src.inc), so
@@ -115,6 +120,7 @@ void shape_kr(int T, int* w, int* s) {
     case 4: shape_of<K, R, 4>(w, s); break;
     case 8: shape_of<K, R, 8>(w, s); break;
     case 16: shape_of<K, R, 16>(w, s); break;
+    case 32: shape_of<K, R, 32>(w, s); break;
     default: *w = 0; *s = 0;
   }
 }
@@ -147,6 +153,7 @@ struct JitKernel {
   int K, R, T;
   uint32_t gens[3];
   bool punct;
+  bool var;  // the instance honouring the traceback / frame variants
   cudaLibrary_t lib[2] = {nullptr, nullptr};
   cudaKernel_t fn[2] = {nullptr, nullptr};
   int smem_granted[2] = {48 * 1024, 48 * 1024};
@@ -162,8 +169,9 @@ void set_err(const std::string& m) {
 
 std::string kernel_name(const JitKernel& k, int smem) {
   char buf[256];
-  std::snprintf(buf, sizeof(buf), "pbvd::pbvd_decode_kernel<pbvd::Code<%d, %uu, %uu, %uu>, %d, %s, %s>", k.K,
-                k.gens[0], k.gens[1], k.gens[2], k.T, k.punct ? "true" : "false", smem ? "true" : "false");
+  std::snprintf(buf, sizeof(buf), "pbvd::pbvd_decode_kernel<pbvd::Code<%d, %uu, %uu, %uu>, %d, %s, %s, %s>", k.K,
+                k.gens[0], k.gens[1], k.gens[2], k.T, k.punct ? "true" : "false", smem ? "true" : "false",
+                k.var ? "true" : "false");
   return buf;
 }
 
@@ -243,13 +251,15 @@ bool jit_available() { return nvrtc().ok; }
 
 const char* jit_last_error() { return g_jit_err; }
 
-int jit_register(int K, int R, const uint32_t* gens, bool punct, KernelEntry* out, int cap) {
+int jit_register(int K, int R, const uint32_t* gens, bool punct, bool var, KernelEntry* out, int cap) {
   if (!jit_available()) return 0;
   std::lock_guard<std::mutex> lk(g_jit_mu);
   const int N = 1 << (K - 1);
   int n = 0;
-  for (int T = 1; T <= 16 && n < cap; T *= 2) {
-    if (T > N / 2 || N / T > 64) continue;
+  // one warp per pair (T = 32) only for codes of 128 states or more (the
+  // 64-state codes use their one-warp latency kernel there)
+  for (int T = 1; T <= 32 && n < cap; T *= 2) {
+    if (T > N / 2 || N / T > 64 || (T == 32 && N < 128)) continue;
     int w = 0, sw = 0;
     shape(K, R, T, &w, &sw);
     if (w <= 0) continue;
@@ -259,6 +269,7 @@ int jit_register(int K, int R, const uint32_t* gens, bool punct, KernelEntry* ou
     k->T = T;
     for (int r = 0; r < 3; ++r) k->gens[r] = r < R ? gens[r] : 0u;
     k->punct = punct;
+    k->var = var;
     g_jit.push_back(k);
     KernelEntry e;
     std::memset(&e, 0, sizeof(e));
@@ -270,7 +281,7 @@ int jit_register(int K, int R, const uint32_t* gens, bool punct, KernelEntry* ou
     e.words_per_stage = w;
     e.scratch_words = sw;
     e.jit = (int)g_jit.size() - 1;
-    e.variants = true;
+    e.variants = var;
     out[n++] = e;
   }
   return n;

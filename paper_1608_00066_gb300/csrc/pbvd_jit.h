@@ -13,9 +13,10 @@ namespace pbvd {
 bool jit_available();
 
 // Writes up to cap entries (one per usable threads-per-pair value) for the
-// code into out and returns how many; 0 without libnvrtc.  Their kernels are
-// compiled on first launch.
-int jit_register(int K, int R, const uint32_t* gens, bool punct, KernelEntry* out, int cap);
+// code into out and returns how many; 0 without libnvrtc.  var: the instances
+// that honour the traceback / frame variants.  Their kernels are compiled on
+// first launch.
+int jit_register(int K, int R, const uint32_t* gens, bool punct, bool var, KernelEntry* out, int cap);
 
 // Launches (compiling first if needed) placement smem (0: survivors in the
 // workspace, 1: in shared memory) of entry jit.  Returns a PBVD_* code.

@@ -7,6 +7,7 @@ pointed at a known launch (skip the warm-up launches, capture the next).
     python -m paper_1608_00066_gb300.prof batch  ...
     python -m paper_1608_00066_gb300.prof stream ...
     python -m paper_1608_00066_gb300.prof frame  [--tune JSON] ...
+    python -m paper_1608_00066_gb300.prof two    ...
 
 Workloads (the benchmark's):
   k7     K=7 r1/2 (171,133) terminated stream, 2^24 info bits, 3 dB, D=512 L=42
@@ -14,6 +15,7 @@ Workloads (the benchmark's):
   batch  10,000 mixed-code frames (K7 r1/2, K7 r3/4, K9 r1/3), one persistent launch
   stream 64 continuous K7 r1/2 streams, 4096 stages per push, one launch per push
   frame  one K7 r1/2 frame of 4096 info bits, 3 dB, D=512 L=42 (latency case)
+  two    the k7 stream with the paper's two-kernel design (K1 then K2 per call)
 
 Prints one line per launch set: the workload, the configuration and the mean
 device time per launch (CUDA events; L2 not flushed, so do not use it as a
@@ -53,6 +55,18 @@ def run_stream_decode(torch, spec, k, ebn0, seed, D, L, tune, warmup, reps):
     cfg = dec.get_config(f.n_stages)
     dec.close()
     return ms, cfg
+
+
+def run_two_kernel(torch, warmup, reps):
+    spec = synth.K7_R12
+    f = synth.make_frame(spec, 1 << 24, 3.0, seed=2003)
+    dec = pbvd.Decoder(spec.K, spec.gens, None, 512, 42)
+    d_llr = torch.from_numpy(f.llr).cuda()
+    d_out = torch.empty((f.n_stages + 7) // 8, dtype=torch.uint8, device="cuda")
+    ms = _events(torch, lambda: pbvd.pbvd_decode_two_kernel(dec.ctx, d_llr.data_ptr(), f.n_stages, d_out.data_ptr()),
+                 warmup, reps)
+    dec.close()
+    return ms, {"design": "two-kernel (K1 + K2)"}
 
 
 def run_batch(torch, warmup, reps):
@@ -97,7 +111,7 @@ def run_streams(torch, warmup, reps, n_streams=64, chunk=4096):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("target", choices=["k7", "k9", "batch", "stream", "frame"])
+    ap.add_argument("target", choices=["k7", "k9", "batch", "stream", "frame", "two"])
     ap.add_argument("--tune", default="", help="JSON kernel configuration for k7 / k9")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reps", type=int, default=3)
@@ -111,6 +125,8 @@ def main(argv=None):
         ms, cfg = run_stream_decode(torch, synth.K9_R13, 1 << 24, 2.0, 3001, 1024, 64, tune, args.warmup, args.reps)
     elif args.target == "frame":
         ms, cfg = run_stream_decode(torch, synth.K7_R12, 4096, 3.0, 1001, 512, 42, tune, args.warmup, args.reps)
+    elif args.target == "two":
+        ms, cfg = run_two_kernel(torch, args.warmup, args.reps)
     elif args.target == "batch":
         ms, cfg = run_batch(torch, args.warmup, args.reps)
     else:
