@@ -230,7 +230,11 @@ typedef struct pbvd_batch_item {
  * length, paired and cut into tiles taken from a device queue) is built on the
  * host and uploaded into a workspace owned by the first item's context, which
  * must therefore not be used by another batch still in flight.  Output ranges
- * must not overlap. */
+ * must not overlap.  Kernel shape: a batch of one code runs that code's own
+ * kernel; a mixed batch runs the wide shape (four threads per pair of blocks
+ * for K=7, sixteen for K=9), or the dense shape (two and eight) when the
+ * configuration of an item's context (pbvd_set_config threads_per_pair)
+ * names the dense shape's value for its code; the bits are the same. */
 PBVD_API int pbvd_decode_batch(const pbvd_batch_item *items, size_t n_items, void *stream);
 
 /* A prepared batch: the work list and workspace of pbvd_decode_batch, kept so

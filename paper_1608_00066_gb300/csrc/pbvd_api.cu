@@ -302,7 +302,11 @@ void host_pipeline_release(pbvd_ctx* c) {
 
 int host_pipeline_setup(pbvd_ctx* c) {
   if (c->hp_ready) return PBVD_OK;
-  PBVD_CUDA(cudaStreamCreateWithFlags(&c->hp_copy, cudaStreamNonBlocking));
+  // the copy stream also runs the unpack kernels of packed input: at the
+  // highest priority their CTAs are dispatched ahead of the decode kernels'
+  int prio_low = 0, prio_high = 0;
+  PBVD_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  PBVD_CUDA(cudaStreamCreateWithPriority(&c->hp_copy, cudaStreamNonBlocking, prio_high));
   for (int l = 0; l < kHostLanes; ++l) {
     PBVD_CUDA(cudaStreamCreateWithFlags(&c->hp_lane[l], cudaStreamNonBlocking));
     PBVD_CUDA(cudaEventCreateWithFlags(&c->hp_done[l], cudaEventDisableTiming));
@@ -365,6 +369,7 @@ struct pbvd_batch {
   size_t h_stage_cap;   // bytes
   cudaEvent_t staged;   // the last upload from h_stage
   int staged_pending;
+  int single;           // the one code slot of the batch (its own kernel), -1 = mixed
 };
 
 namespace {
@@ -410,7 +415,22 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
                 pbvd_batch** out) {
   Registry& reg = registry();
   if (reg.batch.empty()) return PBVD_EUNSUPPORTED;
-  const int entry = 0;
+  // the kernel shape: the dense one (entry 1) when a context of the batch
+  // asks for its threads-per-pair, else the wide default (entry 0)
+  int entry = 0;
+  if (reg.batch.size() > 1) {
+    for (size_t i = 0; i < n_items; ++i) {
+      const pbvd_ctx* c = items[i].ctx;
+      if (!c) continue;
+      for (int s = 0; s < kBatchSlots; ++s) {
+        const BatchKernelEntry& d = reg.batch[1];
+        if (d.K[s] == c->K && d.R[s] == c->R && d.punct[s] == (c->P != 0) &&
+            c->cfg.threads_per_pair == d.T[s] && reg.batch[0].T[s] != d.T[s])
+          entry = 1;
+      }
+      if (entry == 1) break;
+    }
+  }
   const BatchKernelEntry& be = reg.batch[entry];
   // map items to code slots; the contexts of a slot must agree on D, L and
   // the puncture pattern
@@ -482,6 +502,21 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
     }
   }
   const int cta = 64;
+  // a batch of one code runs that code's own kernel; mixed batches the
+  // combined one
+  int single = -1, used = 0;
+  for (int s = 0; s < kBatchSlots; ++s)
+    if (slot_ctx[s]) {
+      ++used;
+      single = s;
+    }
+  if (used != 1) single = -1;
+  int Ts[kBatchSlots], scr[kBatchSlots], wps[kBatchSlots];
+  for (int s = 0; s < kBatchSlots; ++s) {
+    Ts[s] = single >= 0 ? be.single_T[s] : be.T[s];
+    scr[s] = single >= 0 ? be.single_scratch_words[s] : be.scratch_words[s];
+    wps[s] = single >= 0 ? be.single_words_per_stage[s] : be.words_per_stage[s];
+  }
   size_t n_pairs_all = 0;
   for (int s = 0; s < kBatchSlots; ++s) n_pairs_all += (pbs[s].size() + 1) / 2;
   std::vector<BatchTile> tiles;
@@ -489,7 +524,7 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
   for (int s = 0; s < kBatchSlots; ++s) {
     const int64_t np = (int64_t)(pbs[s].size() + 1) / 2;
     if (np == 0) continue;
-    const int groups = cta / be.T[s];
+    const int groups = cta / Ts[s];
     int64_t first_pair = 0;
     for (int q = 0; q < s; ++q) first_pair += (int64_t)(pbs[q].size() + 1) / 2;
     for (int64_t t = 0; t < np; t += groups) {
@@ -499,7 +534,7 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
       tl.first = first_pair + t;
       tiles.push_back(tl);
       // pairs are sorted, so the tile's first pair is its longest
-      tile_cost.push_back((int64_t)pbs[s][(size_t)(2 * t)].len * (1 << (be.K[s] - 1)) * be.T[s] / 2);
+      tile_cost.push_back((int64_t)pbs[s][(size_t)(2 * t)].len * (1 << (be.K[s] - 1)) * Ts[s] / 2);
     }
   }
   // longest tiles first for the dynamic tile queue
@@ -516,25 +551,32 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
   b->device = dev;
   b->entry = entry;
   b->cta = cta;
+  b->single = single;
   size_t smem = 0;
   int gmax = 0;
   for (int s = 0; s < kBatchSlots; ++s) {
-    const int groups = cta / be.T[s];
-    smem = std::max(smem, (size_t)groups * be.scratch_words[s] * 4);
+    if (single >= 0 && s != single) continue;
+    const int groups = cta / Ts[s];
+    smem = std::max(smem, (size_t)groups * scr[s] * 4);
     gmax = std::max(gmax, groups);
   }
   b->smem = smem;
   int rc = PBVD_OK;
-  {
-    std::lock_guard<std::mutex> lk(g_reg_mu);
-    if ((int)smem > reg.batch_smem_set[entry]) {
-      cudaError_t e = be.set_max_smem((int)smem);
-      if (e != cudaSuccess) return cuda_fail(e);
-      reg.batch_smem_set[entry] = (int)smem;
-    }
-  }
   int per_sm = 0;
-  PBVD_CUDA(be.occupancy(&per_sm, cta, smem));
+  if (single < 0) {
+    {
+      std::lock_guard<std::mutex> lk(g_reg_mu);
+      if ((int)smem > reg.batch_smem_set[entry]) {
+        cudaError_t e = be.set_max_smem((int)smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        reg.batch_smem_set[entry] = (int)smem;
+      }
+    }
+    PBVD_CUDA(be.occupancy(&per_sm, cta, smem));
+  } else {
+    if (smem > 48 * 1024) PBVD_CUDA(be.single_set_max_smem(single, (int)smem));
+    PBVD_CUDA(be.single_occupancy(single, &per_sm, cta, smem));
+  }
   if (per_sm < 1) return PBVD_EUNSUPPORTED;
   const int grid_cap = per_sm * std::max(1, c0->sm_count - reserve_sms);
   b->grid = std::max(1, std::min<int>(grid_cap, (int)std::max<size_t>(tiles.size(), 1)));
@@ -545,7 +587,7 @@ int batch_build(const pbvd_batch_item* items, size_t n_items, void* stream, pbvd
   size_t jmax = 0;
   for (int s = 0; s < kBatchSlots; ++s)
     if (slot_ctx[s]) {
-      rs_max = std::max(rs_max, be.words_per_stage[s]);
+      rs_max = std::max(rs_max, wps[s]);
       jmax = std::max(jmax, (size_t)(slot_ctx[s]->D + slot_ctx[s]->L));
     }
   const size_t surv = jmax * (size_t)n_slots * rs_max * 4;
@@ -1057,7 +1099,10 @@ int pbvd_batch_run(pbvd_batch* b, void* stream) {
   if (b->args.ntiles == 0) return PBVD_OK;
   PBVD_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st));
   const BatchKernelEntry& be = registry().batch[b->entry];
-  PBVD_CUDA(be.launch(b->args, b->grid, b->cta, b->smem, st));
+  if (b->single >= 0)
+    PBVD_CUDA(be.single_launch(b->args, b->single, b->grid, b->cta, b->smem, st));
+  else
+    PBVD_CUDA(be.launch(b->args, b->grid, b->cta, b->smem, st));
   return PBVD_OK;
 }
 

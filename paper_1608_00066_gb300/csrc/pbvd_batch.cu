@@ -51,20 +51,90 @@ __global__ void __launch_bounds__(256, 1) pbvd_batch_kernel(const BatchArgs b) {
   }
 }
 
-#define PBVD_BATCH_ARGS K7, 2, false, K7, 2, true, K9, 8, false
+// Two shapes of the mixed-code kernel.  Wide (the default): K=7 paths at
+// four threads per pair of blocks, K=9 at sixteen; its pairs are few and long
+// in a batch of short frames, and more threads per pair shorten the chains
+// that end the launch (measured fastest for the 10,000-frame mixed batch).
+// Dense: K=7 at two threads per pair, K=9 at eight, fewer instructions per
+// butterfly; faster where batches of long frames run several at a time and
+// fill the GPU between them (the serving loop).
+#define PBVD_BATCH_WIDE K7, 4, false, K7, 4, true, K9, 16, false
+#define PBVD_BATCH_DENSE K7, 2, false, K7, 2, true, K9, 8, false
 
+template <class C0, int T0, bool P0, class C1, int T1, bool P1, class C2, int T2, bool P2>
 cudaError_t launch_batch(const BatchArgs& a, int grid, int cta, size_t smem, cudaStream_t s) {
-  pbvd_batch_kernel<PBVD_BATCH_ARGS><<<grid, cta, smem, s>>>(a);
+  pbvd_batch_kernel<C0, T0, P0, C1, T1, P1, C2, T2, P2><<<grid, cta, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+template <class C0, int T0, bool P0, class C1, int T1, bool P1, class C2, int T2, bool P2>
 cudaError_t batch_max_smem(int bytes) {
-  return cudaFuncSetAttribute(pbvd_batch_kernel<PBVD_BATCH_ARGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(pbvd_batch_kernel<C0, T0, P0, C1, T1, P1, C2, T2, P2>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <class C0, int T0, bool P0, class C1, int T1, bool P1, class C2, int T2, bool P2>
+cudaError_t batch_occupancy(int* blocks, int cta, size_t smem) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pbvd_batch_kernel<C0, T0, P0, C1, T1, P1, C2, T2, P2>,
+                                                       cta, smem);
+}
+
+// Batches of a single code: one persistent kernel with only that code's
+// path, so that it gets that path's register budget (eight 64-thread CTAs
+// per SM) instead of the largest of three.
+template <class C, int T, bool PUNCT>
+__global__ void __launch_bounds__(64, 8) pbvd_batch_single_kernel(const BatchArgs b, const int slot) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(b.counter, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    __syncthreads();
+    if (tile >= b.ntiles) break;
+    const BatchTile t = b.tiles[tile];
+    run_tile<C, T, PUNCT>(b.code[slot], b, t, smem);
+  }
+}
+
+#define PBVD_SINGLE0 K7, 4, false
+#define PBVD_SINGLE1 K7, 4, true
+#define PBVD_SINGLE2 K9, 8, false
+
+cudaError_t launch_single(const BatchArgs& a, int slot, int grid, int cta, size_t smem, cudaStream_t s) {
+  if (slot == 0)
+    pbvd_batch_single_kernel<PBVD_SINGLE0><<<grid, cta, smem, s>>>(a, 0);
+  else if (slot == 1)
+    pbvd_batch_single_kernel<PBVD_SINGLE1><<<grid, cta, smem, s>>>(a, 1);
+  else
+    pbvd_batch_single_kernel<PBVD_SINGLE2><<<grid, cta, smem, s>>>(a, 2);
+  return cudaGetLastError();
+}
+
+cudaError_t single_max_smem(int slot, int bytes) {
+  if (slot == 0)
+    return cudaFuncSetAttribute(pbvd_batch_single_kernel<PBVD_SINGLE0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes);
+  if (slot == 1)
+    return cudaFuncSetAttribute(pbvd_batch_single_kernel<PBVD_SINGLE1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes);
+  return cudaFuncSetAttribute(pbvd_batch_single_kernel<PBVD_SINGLE2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               bytes);
 }
 
-cudaError_t batch_occupancy(int* blocks, int cta, size_t smem) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pbvd_batch_kernel<PBVD_BATCH_ARGS>, cta, smem);
+cudaError_t single_occupancy(int slot, int* blocks, int cta, size_t smem) {
+  if (slot == 0)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pbvd_batch_single_kernel<PBVD_SINGLE0>, cta, smem);
+  if (slot == 1)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pbvd_batch_single_kernel<PBVD_SINGLE1>, cta, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pbvd_batch_single_kernel<PBVD_SINGLE2>, cta, smem);
+}
+
+template <class C, int T, bool P>
+void fill_single(BatchKernelEntry& e, int s) {
+  e.single_T[s] = T;
+  e.single_words_per_stage[s] = record_words_per_stage<C, T>();
+  e.single_scratch_words[s] = scratch_words_per_group<C, T>();
 }
 
 template <class C, int T, bool P>
@@ -78,17 +148,30 @@ void fill_slot(BatchKernelEntry& e, int s) {
   e.scratch_words[s] = scratch_words_per_group<C, T>();
 }
 
-int register_batch(BatchKernelEntry* out, int cap) {
-  if (cap < 1) return 0;
+template <class C0, int T0, bool P0, class C1, int T1, bool P1, class C2, int T2, bool P2>
+BatchKernelEntry make_batch_entry() {
   BatchKernelEntry e;
-  fill_slot<K7, 2, false>(e, 0);
-  fill_slot<K7, 2, true>(e, 1);
-  fill_slot<K9, 8, false>(e, 2);
-  e.launch = &launch_batch;
-  e.set_max_smem = &batch_max_smem;
-  e.occupancy = &batch_occupancy;
-  out[0] = e;
-  return 1;
+  fill_slot<C0, T0, P0>(e, 0);
+  fill_slot<C1, T1, P1>(e, 1);
+  fill_slot<C2, T2, P2>(e, 2);
+  e.launch = &launch_batch<C0, T0, P0, C1, T1, P1, C2, T2, P2>;
+  e.set_max_smem = &batch_max_smem<C0, T0, P0, C1, T1, P1, C2, T2, P2>;
+  e.occupancy = &batch_occupancy<C0, T0, P0, C1, T1, P1, C2, T2, P2>;
+  fill_single<PBVD_SINGLE0>(e, 0);
+  fill_single<PBVD_SINGLE1>(e, 1);
+  fill_single<PBVD_SINGLE2>(e, 2);
+  e.single_launch = &launch_single;
+  e.single_set_max_smem = &single_max_smem;
+  e.single_occupancy = &single_occupancy;
+  return e;
+}
+
+// Entry 0: the wide shape (default); entry 1: the dense shape.
+int register_batch(BatchKernelEntry* out, int cap) {
+  int n = 0;
+  if (n < cap) out[n++] = make_batch_entry<PBVD_BATCH_WIDE>();
+  if (n < cap) out[n++] = make_batch_entry<PBVD_BATCH_DENSE>();
+  return n;
 }
 
 }  // namespace pbvd

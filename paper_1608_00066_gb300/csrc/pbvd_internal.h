@@ -122,6 +122,9 @@ struct StreamKernelEntry {
 
 using BatchLaunchFn = cudaError_t (*)(const BatchArgs& a, int grid, int cta, size_t smem, cudaStream_t s);
 using BatchOccFn = cudaError_t (*)(int* blocks_per_sm, int cta, size_t smem);
+using BatchSlotLaunchFn = cudaError_t (*)(const BatchArgs& a, int slot, int grid, int cta, size_t smem, cudaStream_t s);
+using BatchSlotOccFn = cudaError_t (*)(int slot, int* blocks_per_sm, int cta, size_t smem);
+using BatchSlotAttrFn = cudaError_t (*)(int slot, int smem_bytes);
 
 // The combined persistent kernel for mixed-code batches.
 struct BatchKernelEntry {
@@ -133,6 +136,13 @@ struct BatchKernelEntry {
   BatchLaunchFn launch;
   AttrFn set_max_smem;
   BatchOccFn occupancy;
+  // batches whose frames are all of one code slot: that slot's own kernel
+  int single_T[kBatchSlots];
+  int single_words_per_stage[kBatchSlots];
+  int single_scratch_words[kBatchSlots];
+  BatchSlotLaunchFn single_launch;
+  BatchSlotAttrFn single_set_max_smem;
+  BatchSlotOccFn single_occupancy;
 };
 
 // Unpacks q-bit soft values [v0, v1) of words into out[v0 .. v1) as int8,

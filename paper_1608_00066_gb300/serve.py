@@ -251,6 +251,8 @@ class ServeConfig:
     reserve_sms: int = 0               # SMs the batch grid leaves to stream pushes
     geometry: Dict[str, tuple] = dataclasses.field(default_factory=lambda: {
         "K7_r1/2": (512, 42), "K7_r3/4": (512, 42), "K9_r1/3": (1024, 64)})
+    # threads per pair of blocks per K, selecting the batch kernel's dense shape
+    dense_threads: Dict[int, int] = dataclasses.field(default_factory=lambda: {7: 2, 9: 8})
 
 
 class _Slot:
@@ -345,6 +347,10 @@ class Server:
         for name in pool.code_names:
             s = specs[name]
             self.decoders[name] = pbvd.Decoder(s.K, s.gens, s.puncture, *cfg.geometry[name])
+            # the dense shape of the mixed-code batch kernel (two threads per
+            # pair for K=7, eight for K=9): several long-frame batches in
+            # flight fill the GPU between them
+            self.decoders[name].set_config(threads_per_pair=cfg.dense_threads[s.K])
         self.ctx_of_code = np.array([self.decoders[nm].ctx for nm in pool.code_names], np.uint64)
         self.host_in = torch.from_numpy(pool.host_in).pin_memory()
         self.host_out = torch.zeros(pool.out_bytes, dtype=torch.uint8).pin_memory()
