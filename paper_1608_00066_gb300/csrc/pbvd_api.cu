@@ -146,6 +146,8 @@ struct pbvd_ctx {
   // pbvd_decode_host: copy stream, compute lanes, events and device buffers
   int hp_ready;
   cudaStream_t hp_copy;
+  cudaStream_t hp_unpack;  // unpacks of packed input, trailing the copies
+  cudaEvent_t hp_unp[64];
   cudaStream_t hp_lane[16];
   cudaEvent_t hp_fork;
   cudaEvent_t hp_in[64];
@@ -279,6 +281,8 @@ constexpr int kHostMaxSegments = 64;
 void host_pipeline_release(pbvd_ctx* c) {
   if (c->hp_ready) {
     cudaStreamDestroy(c->hp_copy);
+    cudaStreamDestroy(c->hp_unpack);
+    for (int i = 0; i < kHostMaxSegments; ++i) cudaEventDestroy(c->hp_unp[i]);
     for (int l = 0; l < kHostLanes; ++l) {
       cudaStreamDestroy(c->hp_lane[l]);
       cudaEventDestroy(c->hp_done[l]);
@@ -302,11 +306,14 @@ void host_pipeline_release(pbvd_ctx* c) {
 
 int host_pipeline_setup(pbvd_ctx* c) {
   if (c->hp_ready) return PBVD_OK;
-  // the copy stream also runs the unpack kernels of packed input: at the
-  // highest priority their CTAs are dispatched ahead of the decode kernels'
+  // packed input is unpacked on a stream of its own, at the highest
+  // priority, so that the copies run back to back and each unpack's CTAs are
+  // dispatched ahead of the decode kernels'
   int prio_low = 0, prio_high = 0;
   PBVD_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
-  PBVD_CUDA(cudaStreamCreateWithPriority(&c->hp_copy, cudaStreamNonBlocking, prio_high));
+  PBVD_CUDA(cudaStreamCreateWithFlags(&c->hp_copy, cudaStreamNonBlocking));
+  PBVD_CUDA(cudaStreamCreateWithPriority(&c->hp_unpack, cudaStreamNonBlocking, prio_high));
+  for (int i = 0; i < kHostMaxSegments; ++i) PBVD_CUDA(cudaEventCreateWithFlags(&c->hp_unp[i], cudaEventDisableTiming));
   for (int l = 0; l < kHostLanes; ++l) {
     PBVD_CUDA(cudaStreamCreateWithFlags(&c->hp_lane[l], cudaStreamNonBlocking));
     PBVD_CUDA(cudaEventCreateWithFlags(&c->hp_done[l], cudaEventDisableTiming));
@@ -993,9 +1000,15 @@ int decode_host_impl(pbvd_ctx* c, const void* h_in, int q, size_t n_stages, uint
       const size_t w0 = v0 / per_word, w1 = std::min(n_words, (v1 + per_word - 1) / per_word);
       PBVD_CUDA(cudaMemcpyAsync(c->hp_words + w0, h_words + w0, (w1 - w0) * 4, cudaMemcpyHostToDevice,
                                 c->hp_copy));
-      PBVD_CUDA(launch_unpack(q, c->hp_words, (int64_t)v0, (int64_t)v1, c->hp_llr, c->hp_copy));
     }
     PBVD_CUDA(cudaEventRecord(c->hp_in[i], c->hp_copy));
+    if (q > 0) {
+      // values [v0, v1) once their words have arrived (in order, so run i
+      // finds every value before v1 unpacked)
+      PBVD_CUDA(cudaStreamWaitEvent(c->hp_unpack, c->hp_in[i], 0));
+      if (v1 > v0) PBVD_CUDA(launch_unpack(q, c->hp_words, (int64_t)v0, (int64_t)v1, c->hp_llr, c->hp_unpack));
+      PBVD_CUDA(cudaEventRecord(c->hp_unp[i], c->hp_unpack));
+    }
   }
   KArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -1016,7 +1029,7 @@ int decode_host_impl(pbvd_ctx* c, const void* h_in, int q, size_t n_stages, uint
   for (int i = 0; i < S; ++i) {
     const int l = i % kHostLanes;
     cudaStream_t st = c->hp_lane[l];
-    PBVD_CUDA(cudaStreamWaitEvent(st, c->hp_in[i], 0));
+    PBVD_CUDA(cudaStreamWaitEvent(st, q > 0 ? c->hp_unp[i] : c->hp_in[i], 0));
     const Run& r = runs[i];
     a.b_first = r.b0;
     a.n_blocks = r.b1;
