@@ -736,18 +736,43 @@ def _full_frame_ber(ebn0: int):
     return ebn0, int((bits[:K_INFO] != f.msg).sum()), time.perf_counter() - t0
 
 
+def _sweep_blocks_worker(job):
+    """Child process: oracle bits of blocks [b0, b1) of a sweep stream."""
+    path, D, L, b0, b1 = job
+    sys.path.insert(0, ROOT)
+    import oracle as orc
+    llr = np.load(path, mmap_mode="r")
+    n = llr.shape[0]
+    out = orc.viterbi_block(7, (0o171, 0o133), np.ascontiguousarray(llr), D, L, blocks=(b0, b1))
+    return b0, out[b0 * D:min(b1 * D, n)].copy()
+
+
+def _oracle_all_blocks(pool, path, n, D, L, parts):
+    """Every block of a sweep stream with the CPU oracle, over the pool."""
+    nb = (n + D - 1) // D
+    step = max(1, (nb + parts - 1) // parts)
+    out = np.zeros(n, dtype=np.uint8)
+    for b0, bits in pool.imap_unordered(_sweep_blocks_worker,
+                                        [(path, D, L, b, min(nb, b + step)) for b in range(0, nb, step)]):
+        out[b0 * D:b0 * D + len(bits)] = bits
+    return out
+
+
 def run_sweep(args):
     """The K=7 r1/2 stream of 2^24 information bits at Eb/N0 = 0..6 dB, each
     decoded with D in {256, 512, 1024, 2048} and L in {35, 42, 64}: device
     throughput (tuned kernel configuration, L2 flushed between steps), bit
     errors of the block decoder, bit errors of the full-frame decoder (CPU,
     in spawned processes) so that the truncation loss of the blocks is shown,
-    and a sampled bit-exact check of every run against the block oracle
-    (first, last and two random blocks)."""
+    and a bit-exact check of every block of every run against the block
+    oracle (the oracle's blocks spread over the host cores)."""
     import multiprocessing as mp
+    import tempfile
     ctx = mp.get_context("spawn")
     pool = ctx.Pool(min(len(SWEEP_EBN0), os.cpu_count() or 1))
     full = pool.map_async(_full_frame_ber, SWEEP_EBN0)
+    cores = os.cpu_count() or 1
+    bpool = ctx.Pool(cores)
     import torch
     import oracle as orc
     from paper_1608_00066_gb300 import build as pbuild
@@ -760,7 +785,9 @@ def run_sweep(args):
     for e in SWEEP_EBN0:
         f = _sweep_frame(e)
         n = f.n_stages
-        llr2 = f.llr.reshape(n, 2)
+        tmp = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
+        tmp.close()
+        np.save(tmp.name, f.llr.reshape(n, 2))
         d_llr = torch.from_numpy(f.llr).cuda()
         d_out = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
         for D in SWEEP_D:
@@ -769,21 +796,18 @@ def run_sweep(args):
                 dec.autotune(d_llr, n, d_out, reps=2)
                 ms = time_decode(dec, d_llr, n, d_out, max(3, args.steps), 2, flush)
                 got = np.unpackbits(d_out.cpu().numpy(), bitorder="little")[:n]
-                nb = (n + D - 1) // D
-                rng = np.random.default_rng(1000 * e + D + L)
-                picks = sorted({0, nb - 1, *(int(x) for x in rng.integers(1, nb - 1, size=2))})
-                exact = True
-                for b in picks:
-                    want = orc.viterbi_block(7, gens, llr2, D, L, blocks=(b, b + 1))
-                    o0, o1 = b * D, min((b + 1) * D, n)
-                    exact &= bool(np.array_equal(got[o0:o1], want[o0:o1]))
+                want = _oracle_all_blocks(bpool, tmp.name, n, D, L, 4 * cores)
+                bad = int((got != want).sum())
                 rows.append({"ebn0_db": e, "D": D, "L": L, "gbps": round(K_INFO / ms / 1e6, 3),
                              "ms": round(ms, 4), "bit_errors": int((got[:K_INFO] != f.msg).sum()),
-                             "kernel_config": dec.get_config(n), "sampled_blocks_exact": exact})
+                             "kernel_config": dec.get_config(n), "all_blocks_exact": bad == 0,
+                             "bits_differing_from_oracle": bad})
                 dec.close()
+        os.unlink(tmp.name)
         del d_llr, d_out
     full_res = {e: (errs, secs) for e, errs, secs in full.get()}
     pool.close()
+    bpool.close()
     for r in rows:
         r["full_frame_bit_errors"] = full_res[r["ebn0_db"]][0]
         r["ber"] = r["bit_errors"] / K_INFO
