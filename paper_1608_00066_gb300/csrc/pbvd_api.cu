@@ -2,6 +2,7 @@
 // selection, workspace management and launches.  No decoding arithmetic runs
 // on the host.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -34,7 +35,11 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 struct Registry {
+  // entries never move (capacity reserved at start); n_entries publishes how
+  // many are complete, so lookups need no lock while codes compiled at run
+  // time are appended
   std::vector<KernelEntry> entries;
+  std::atomic<size_t> n_entries{0};
   std::vector<int> smem_set;  // max dynamic smem already granted per entry and survivor placement
   std::vector<BatchKernelEntry> batch;
   std::vector<int> batch_smem_set;
@@ -57,6 +62,7 @@ Registry& registry() {
     reg.entries.assign(buf, buf + n);
     reg.smem_set.reserve(2 * 4096);
     reg.smem_set.assign(2 * n, 48 * 1024);
+    reg.n_entries.store((size_t)n, std::memory_order_release);
     BatchKernelEntry bb[4];
     const int nb = register_batch(bb, 4);
     reg.batch.assign(bb, bb + nb);
@@ -73,7 +79,8 @@ std::mutex g_reg_mu;
 // by pbvd_set_mode), else the plain ones.
 int find_entry(int K, int R, const uint32_t* gens, int T, bool punct, bool var = false) {
   Registry& reg = registry();
-  for (size_t i = 0; i < reg.entries.size(); ++i) {
+  const size_t count = reg.n_entries.load(std::memory_order_acquire);
+  for (size_t i = 0; i < count; ++i) {
     const KernelEntry& e = reg.entries[i];
     if (e.K != K || e.R != R || e.T != T || e.punct != punct) continue;
     if (e.variants != var) continue;
@@ -105,6 +112,7 @@ int ensure_code_kernels(int K, int R, const uint32_t* gens, bool punct, bool var
     reg.smem_set.push_back(48 * 1024);
     reg.smem_set.push_back(48 * 1024);
   }
+  reg.n_entries.store(reg.entries.size(), std::memory_order_release);
   return 1;
 }
 
