@@ -312,7 +312,12 @@ PBVD_API int pbvd_autotune(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages, 
  * make it outside stream capture; the address is kept until the process
  * exits, so do not reset the device (cudaDeviceReset) while using the
  * library.  All calls share the array: calls whose work overlaps on the GPU
- * (other streams, other host threads) race on it. */
+ * (other streams, other host threads) race on it.  Kernels the library
+ * compiles at run time (codes without a built-in kernel, the decoding
+ * variants of pbvd_set_mode) allocate device memory when they are first
+ * loaded, so this call returns PBVD_EUNSUPPORTED until pbvd_decode has
+ * launched the same kernel once (the same code, mode and configuration, and
+ * a stream length for which the automatic configuration is the same). */
 PBVD_API int pbvd_decode_noalloc(pbvd_ctx *ctx, const int8_t *d_llr, size_t n_stages,
                                  uint8_t *d_out, void *stream);
 

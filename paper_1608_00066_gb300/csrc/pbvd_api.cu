@@ -1221,6 +1221,12 @@ int pbvd_decode_noalloc(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8
     if (rc != PBVD_OK) return rc;
   }
   if (!p.smem_surv && p.surv_bytes > kNoAllocSurvivorBytes) return PBVD_EINVAL;
+  // a kernel compiled at run time must be loaded already: loading it
+  // allocates device memory for its code
+  {
+    const KernelEntry& ej = registry().entries[p.entry];
+    if (ej.jit >= 0 && !jit_loaded(ej.jit, p.smem_surv ? 1 : 0)) return PBVD_EUNSUPPORTED;
+  }
   uint32_t* surv = nullptr;
   rc = noalloc_survivors(dev, &surv);
   if (rc != PBVD_OK) return rc;

@@ -310,6 +310,12 @@ int jit_launch(int jit, int smem, const KArgs& a, int grid, int cta, size_t smem
   return PBVD_OK;
 }
 
+bool jit_loaded(int jit, int smem) {
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  JitKernel* k = get(jit);
+  return k && k->fn[smem] != nullptr;
+}
+
 int jit_set_max_smem(int jit, int smem, int bytes) {
   std::lock_guard<std::mutex> lk(g_jit_mu);
   JitKernel* k = get(jit);

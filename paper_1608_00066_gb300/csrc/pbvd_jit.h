@@ -22,6 +22,9 @@ int jit_register(int K, int R, const uint32_t* gens, bool punct, bool var, Kerne
 // workspace, 1: in shared memory) of entry jit.  Returns a PBVD_* code.
 int jit_launch(int jit, int smem, const KArgs& a, int grid, int cta, size_t smem_bytes, cudaStream_t s);
 
+// Whether placement smem of entry jit is compiled and loaded already.
+bool jit_loaded(int jit, int smem);
+
 // Raises the kernel's dynamic shared-memory limit (compiling first if needed).
 int jit_set_max_smem(int jit, int smem, int bytes);
 

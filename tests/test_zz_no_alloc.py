@@ -122,3 +122,22 @@ def test_noalloc_keeps_shared_memory_survivors_for_short_frames():
     for _ in range(2):
         assert np.array_equal(_decode(pbvd.pbvd_decode_noalloc, dec, f.llr, f.n_stages), want)
     dec.close()
+
+
+def test_noalloc_needs_run_time_kernels_loaded_first():
+    """A code without a built-in kernel is compiled at run time, and loading
+    that kernel allocates device memory: the allocation-free call refuses it
+    until pbvd_decode has loaded it, then gives the same bits."""
+    # a code no other test decodes, so that its kernel is not loaded yet even
+    # when the whole suite ran before in this process
+    spec = synth.CodeSpec("K6_65_57", 6, (0o65, 0o57))
+    dec = pbvd.Decoder(spec.K, spec.gens, None, 256, 36)
+    dec.set_config(threads_per_pair=4, cta_threads=64, survivors_in_smem=0)
+    f = synth.make_frame(spec, 20000, 2.0, seed=77)
+    with pytest.raises(pbvd.PbvdError) as ei:
+        _decode(pbvd.pbvd_decode_noalloc, dec, f.llr, f.n_stages)
+    assert ei.value.code == pbvd.PBVD_EUNSUPPORTED
+    want = _decode(pbvd.pbvd_decode, dec, f.llr, f.n_stages)
+    for _ in range(2):
+        assert np.array_equal(_decode(pbvd.pbvd_decode_noalloc, dec, f.llr, f.n_stages), want)
+    dec.close()
