@@ -1040,6 +1040,34 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
         g[0] = g1[0];
       }
     }
+    // One parallel round first: every guessed segment whose entry state
+    // differs from the exit state of the first walk of the segment above is
+    // walked again from that state, all such segments at once in their own
+    // lanes.  The exit of a segment above is exact unless that segment was
+    // itself walked again and ended elsewhere, which the top-down check below
+    // finds (and walks again, one segment after another) as before.
+    for (int pb = 0; pb < (hasB ? 2 : 1); ++pb) {
+      const PbRun& gp = pb ? gB : gA;
+      const int jend_p = pb ? jB : jA;
+      const int seg_p = BOTH ? seg : (((jend_p + 1 + SPB - 1) / SPB) + 7) & ~7;
+      const int top = jend_p / seg_p;
+      const int base = BOTH ? 0 : pb * SPB;
+      const int c = BOTH ? pb : 0;
+      const int q = tau - base;
+      const int above = __shfl_sync(gmask, c ? psi[1] : psi[0], (tau + 1) & (T - 1), T);
+      const bool redo = (BOTH || xb == pb) && q < top && above != (c ? g[1] : g[0]);
+      if (redo) {
+        const int lo_q = q * seg_p, hi_q = min(jend_p, lo_q + seg_p - 1);
+        int p2[1] = {above}, g2[1];
+        const int emit_top[1] = {min(hi_q, gp.nout - 1)};
+        const int je[1] = {jend_p};
+        const int x[1] = {pb};
+        const int nout[1] = {gp.nout};
+        uint8_t* const dst[1] = {gp.dst};
+        tb_walk_any<C, T, SMEM, 1>(a, gslot, svs, ring, L, hi_q, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
+        if (c) { psi[1] = p2[0]; g[1] = above; } else { psi[0] = p2[0]; g[0] = above; }
+      }
+    }
     // top-down check of the guessed segments of each PB: segment q is exact
     // if the state its walk held at record hi_q equals the exact exit state
     // of segment q + 1; otherwise it is walked again from that state (rare).
