@@ -208,6 +208,22 @@ PBVD_API int pbvd_decode_packed(pbvd_ctx *ctx, const uint32_t *d_words, int q, s
 PBVD_API int pbvd_decode_host_packed(pbvd_ctx *ctx, const uint32_t *h_words, int q, size_t n_stages,
                                      uint8_t *h_out, int segments, void *stream);
 
+/* pbvd_decode_packed with 8-bit path metrics (Sec. IV-C: with q-bit soft
+ * values the branch metrics are at most BMmax = 2QR, Q = 2^{q-1} - 1, or 1
+ * for q = 1, and the metrics of a block stay within (K - 1) BMmax of each
+ * other, so they fit in bytes when K * BMmax < 127): four blocks per 32-bit
+ * register, one thread per four blocks.  Same input format as
+ * pbvd_decode_packed and the same decoded bits as that call, i.e. as the
+ * block-based decoder on the q-bit branch metric.
+ * Built for the K=7 (171,133) and (171,165,133) codes and the K=5 (23,35)
+ * code, unpunctured, without pbvd_set_mode flags; q <= 3 for R = 2 at K = 7
+ * and K = 5 and for R = 3 at K = 7.  PBVD_EUNSUPPORTED otherwise.  Grows two
+ * context buffers on first use of a larger size (the values regrouped four
+ * blocks to a word, 4 R min(D + 2L, n) bytes per four blocks, and the survivor
+ * records, min(D + 2L, n) 2^{K-1} / 2 bytes per four blocks); asynchronous. */
+PBVD_API int pbvd_decode_packed_pm8(pbvd_ctx *ctx, const uint32_t *d_words, int q, size_t n_stages,
+                                    uint8_t *d_out, void *stream);
+
 /* Number of soft values d_llr must hold for n_stages stages. */
 PBVD_API int pbvd_llr_count(const pbvd_ctx *ctx, size_t n_stages, size_t *count);
 

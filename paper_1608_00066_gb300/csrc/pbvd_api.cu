@@ -13,6 +13,7 @@
 
 #include "pbvd.h"
 #include "pbvd_internal.h"
+#include "pbvd_pm8.h"
 #include "pbvd_jit.h"
 
 using namespace pbvd;
@@ -173,6 +174,10 @@ struct pbvd_ctx {
   int mode;              // PBVD_MODE_* flags
   int8_t* tb_ext;        // tail-biting: the frame with L wrapped stages on each side
   size_t tb_ext_cap;
+  uint32_t* pm8_in;      // pbvd_decode_packed_pm8: gathered values of the quads
+  size_t pm8_in_cap;
+  uint32_t* pm8_surv;    // pbvd_decode_packed_pm8: survivor records
+  size_t pm8_surv_cap;
 };
 
 namespace {
@@ -766,9 +771,11 @@ int pbvd_create(pbvd_ctx** out, int K, int R, const uint32_t* gens, const uint8_
 void pbvd_destroy(pbvd_ctx* c) {
   if (!c) return;
   if (c->batch) pbvd_batch_destroy(c->batch);
-  if (c->work || c->hp_ready) cudaDeviceSynchronize();
+  if (c->work || c->hp_ready || c->pm8_surv) cudaDeviceSynchronize();
   if (c->work) cudaFree(c->work);
   if (c->tb_ext) cudaFree(c->tb_ext);
+  if (c->pm8_in) cudaFree(c->pm8_in);
+  if (c->pm8_surv) cudaFree(c->pm8_surv);
   host_pipeline_release(c);
   delete c;
 }
@@ -1083,6 +1090,26 @@ int pbvd_decode_packed(pbvd_ctx* c, const uint32_t* d_words, int q, size_t n_sta
   if (rc != PBVD_OK) return rc;
   PBVD_CUDA(launch_unpack(q, d_words, 0, (int64_t)count, c->pk_vals, static_cast<cudaStream_t>(stream)));
   return pbvd_decode(c, c->pk_vals, n_stages, d_out, stream);
+}
+
+int pbvd_decode_packed_pm8(pbvd_ctx* c, const uint32_t* d_words, int q, size_t n_stages, uint8_t* d_out,
+                           void* stream) {
+  if (!c || !d_words || !d_out || n_stages == 0 || q < 1 || q > 8) return PBVD_EINVAL;
+  if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
+  if (c->P != 0 || c->mode != 0) return PBVD_EUNSUPPORTED;
+  pbvd::Pm8Plan plan;
+  if (pbvd::pm8_plan(c->K, c->R, c->gens, q, &plan) != 0) return PBVD_EUNSUPPORTED;
+  int64_t I = 0, nquads = 0;
+  size_t in_words = 0, surv_words = 0;
+  pbvd::pm8_sizes(c->K, c->R, (int64_t)n_stages, c->D, c->L, &I, &nquads, &in_words, &surv_words);
+  if ((nquads + 31) / 32 > INT32_MAX) return PBVD_EINVAL;
+  int rc = grow_device(&c->pm8_in, &c->pm8_in_cap, in_words * 4);
+  if (rc != PBVD_OK) return rc;
+  rc = grow_device(&c->pm8_surv, &c->pm8_surv_cap, surv_words * 4);
+  if (rc != PBVD_OK) return rc;
+  PBVD_CUDA(pbvd::pm8_launch(plan, c->K, c->R, d_words, (int64_t)n_stages, c->D, c->L, c->pm8_in, c->pm8_surv,
+                             d_out, static_cast<cudaStream_t>(stream)));
+  return PBVD_OK;
 }
 
 int pbvd_decode_batch(const pbvd_batch_item* items, size_t n_items, void* stream) {

@@ -37,7 +37,7 @@ EXPORTS = (
     "pbvd_stream_open", "pbvd_stream_push", "pbvd_stream_push_many", "pbvd_stream_close",
     "pbvd_stream_released", "pbvd_stream_destroy", "pbvd_batch_update", "pbvd_decode_host",
     "pbvd_decode_packed", "pbvd_decode_host_packed", "pbvd_set_mode", "pbvd_get_mode",
-    "pbvd_decode_two_kernel",
+    "pbvd_decode_two_kernel", "pbvd_decode_packed_pm8",
 )
 
 PBVD_MODE_ARGMIN = 1
@@ -100,6 +100,8 @@ def load(path: Optional[str] = None):
         lib.pbvd_get_mode.restype = I
         lib.pbvd_decode_packed.argtypes = [V, V, I, SZ, V, V]
         lib.pbvd_decode_packed.restype = I
+        lib.pbvd_decode_packed_pm8.argtypes = [V, V, I, SZ, V, V]
+        lib.pbvd_decode_packed_pm8.restype = I
         lib.pbvd_decode_host_packed.argtypes = [V, V, I, SZ, V, I, V]
         lib.pbvd_decode_host_packed.restype = I
         lib.pbvd_llr_count.argtypes = [V, SZ, ctypes.POINTER(SZ)]
@@ -208,6 +210,13 @@ def pbvd_decode_packed(ctx: int, d_words: int, q: int, n_stages: int, d_out: int
     """Decode of q-bit soft values packed floor(32/q) to a 32-bit word
     (device pointers; q = 1 is hard decision)."""
     _check(load().pbvd_decode_packed(ctx, d_words, q, n_stages, d_out, stream or None), "pbvd_decode_packed")
+
+
+def pbvd_decode_packed_pm8(ctx: int, d_words: int, q: int, n_stages: int, d_out: int, stream: int = 0) -> None:
+    """pbvd_decode_packed with 8-bit path metrics, four blocks per register
+    (device pointers; small q only, PBVD_EUNSUPPORTED otherwise)."""
+    _check(load().pbvd_decode_packed_pm8(ctx, d_words, q, n_stages, d_out, stream or None),
+           "pbvd_decode_packed_pm8")
 
 
 def pbvd_decode_host_packed(ctx: int, h_words: int, q: int, n_stages: int, h_out: int, segments: int = 0,
@@ -442,6 +451,24 @@ class Decoder:
         else:
             s = stream if stream is not None else torch.cuda.current_stream()
             pbvd_decode_host_packed(self.ctx, words.data_ptr(), q, n_stages, out.data_ptr(), 0, s.cuda_stream)
+        return out
+
+    def decode_packed_pm8(self, words, q: int, n_stages: int, out=None, stream=None):
+        """decode_packed on the GPU with 8-bit path metrics (same bits)."""
+        import torch
+        if words.dtype not in (torch.int32, torch.uint32) or not words.is_contiguous() or not words.is_cuda:
+            raise ValueError("words must be a contiguous 32-bit CUDA tensor")
+        m = 32 // q
+        need = (self.llr_count(n_stages) + m - 1) // m
+        if words.numel() < need:
+            raise ValueError("words holds %d words, %d needed" % (words.numel(), need))
+        nbytes = (n_stages + 7) // 8
+        if out is None:
+            out = torch.empty(nbytes, dtype=torch.uint8, device=words.device)
+        if out.numel() < nbytes or out.dtype != torch.uint8 or not out.is_cuda:
+            raise ValueError("out must be a uint8 CUDA tensor of %d bytes" % nbytes)
+        s = stream if stream is not None else torch.cuda.current_stream(words.device)
+        pbvd_decode_packed_pm8(self.ctx, words.data_ptr(), q, n_stages, out.data_ptr(), s.cuda_stream)
         return out
 
 

@@ -133,6 +133,54 @@ def test_scaled_int8_values_decode_the_same(q):
         assert np.array_equal(oracle.viterbi_block(K, gens, scaled, D, L), want), (q, K)
 
 
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+@pytest.mark.parametrize("K, gens", [(7, K7), (5, (0o23, 0o35)), (7, (0o171, 0o165, 0o133))])
+def test_metric_spread_bound(q, K, gens):
+    """The bound that 8-bit path metrics rest on, read off the oracle's own
+    metrics: with the q-bit branch metric (in [0, 2QR]) every state is reached
+    from the best state of v = K - 1 stages earlier, so from stage v - 1 on
+    (known start, every state reachable) max - min <= v * 2QR, and the
+    smallest metric grows by at most 2QR per stage.  The oracle's full-frame
+    form runs on the scaled int8 values (s * BM_q plus the same offset on
+    every branch of a stage), so metric differences are s times the q-bit
+    ones.  Noisy frames and words of uniformly random bits (every q-bit code,
+    the clamped -Q-1 included); the bound is also reached or approached, so a
+    looser constant would not pass unnoticed."""
+    Q = oracle.q_max(q)
+    s = 127 // Q
+    R = len(gens)
+    v = K - 1
+    bm_span = 2 * Q * R
+    offset = (127 - s * Q) * R
+    spec = synth.CodeSpec("t", K, tuple(gens))
+    rng = np.random.default_rng(q * 31 + K + R)
+    m = 32 // q
+    worst = 0
+    for kind in ("noisy", "random", "clean"):
+        if kind == "noisy":
+            f = synth.make_packed_frame(spec, 3000, 0.0, q, seed=q + 7 * K)
+            n = f.n_stages
+            vals = oracle.unpack_soft(q, f.words, n * R).reshape(n, R)
+        elif kind == "random":
+            n = 3000
+            words = rng.integers(0, 1 << 32, size=(n * R + m - 1) // m, dtype=np.uint64).astype(np.uint32)
+            vals = oracle.unpack_soft(q, words, n * R).reshape(n, R)
+        else:
+            # the all-zero codeword received without noise: every other path
+            # pays for each of its code bits, which spreads the metrics most
+            n = 200
+            vals = np.full((n, R), Q, dtype=np.int8)
+        scaled = (np.maximum(vals.astype(np.int16), -Q) * s).astype(np.int8)
+        _, _, _, pm = oracle.viterbi_full(K, gens, scaled, want_trace=True)
+        spread = (pm.max(axis=1) - pm.min(axis=1))[v - 1:]
+        assert np.all(spread % s == 0)
+        assert int(spread.max()) // s <= v * bm_span, (kind, int(spread.max()) // s)
+        worst = max(worst, int(spread.max()) // s)
+        grow = np.diff(pm.min(axis=1)) - offset
+        assert np.all(grow >= 0) and np.all(grow <= s * bm_span), kind
+    assert 3 * worst >= 2 * v * bm_span, worst
+
+
 def test_hard_decision_worked_example(golden_dir):
     """The hand-traced K=3 example read as hard decisions: every metric is the
     traced one divided by 127 (254 per differing bit becomes 2), the survivor
