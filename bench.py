@@ -659,12 +659,21 @@ def run_quantised(args, dec, stream, flush):
                             max(5, args.steps), max(3, args.warmup), flush, stream)
         bits_dev = np.unpackbits(o_dev.cpu().numpy(), bitorder="little")[:K_INFO]
         bits_host = np.unpackbits(o_host.numpy(), bitorder="little")[:K_INFO]
-        rows.append({"q": q, "values_per_word": 32 // q, "h2d_bytes_per_step": int(f.words.nbytes),
-                     "device_gbps": round(K_INFO / dev_ms / 1e6, 3), "e2e_gbps": round(K_INFO / host_ms / 1e6, 3),
-                     "ber": float((bits_dev != f.msg).mean()),
-                     "host_equals_device": bool(np.array_equal(bits_dev, bits_host))})
+        row = {"q": q, "values_per_word": 32 // q, "h2d_bytes_per_step": int(f.words.nbytes),
+               "device_gbps": round(K_INFO / dev_ms / 1e6, 3), "e2e_gbps": round(K_INFO / host_ms / 1e6, 3),
+               "ber": float((bits_dev != f.msg).mean()),
+               "host_equals_device": bool(np.array_equal(bits_dev, bits_host))}
+        if q <= 3:
+            # 8-bit path metrics, four blocks per register (K * 2QR < 127)
+            o8 = torch.empty_like(o_dev)
+            pm8_ms = _event_ms(lambda: dec.decode_packed_pm8(w_dev, q, n, out=o8, stream=stream),
+                               max(5, args.steps), max(3, args.warmup), flush, stream)
+            row["pm8_device_gbps"] = round(K_INFO / pm8_ms / 1e6, 3)
+            row["pm8_equals_16bit"] = bool(torch.equal(o8, o_dev))
+        rows.append(row)
     return {"workload": "K7 r1/2 stream, 2^24 info bits, 3 dB, D=512 L=42; q-bit soft values packed "
-                        "floor(32/q) per word (q = 1: hard decision)", "rows": rows}
+                        "floor(32/q) per word (q = 1: hard decision); pm8: the same words decoded with 8-bit "
+                        "path metrics", "rows": rows}
 
 
 def time_decode(dec, d_llr, n, d_out, steps: int, warmup: int, flush):

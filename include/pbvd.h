@@ -212,7 +212,10 @@ PBVD_API int pbvd_decode_host_packed(pbvd_ctx *ctx, const uint32_t *h_words, int
  * values the branch metrics are at most BMmax = 2QR, Q = 2^{q-1} - 1, or 1
  * for q = 1, and the metrics of a block stay within (K - 1) BMmax of each
  * other, so they fit in bytes when K * BMmax < 127): four blocks per 32-bit
- * register, one thread per four blocks.  Same input format as
+ * register, one or two threads per four blocks (two split the states of a
+ * 64-state code between them; the context's pbvd_set_config threads_per_pair
+ * picks 1 or 2, otherwise two while there are fewer than 64 four-block
+ * groups per SM).  Same input format as
  * pbvd_decode_packed and the same decoded bits as that call, i.e. as the
  * block-based decoder on the q-bit branch metric.
  * Built for the K=7 (171,133) and (171,165,133) codes and the K=5 (23,35)

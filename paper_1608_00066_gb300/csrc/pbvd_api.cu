@@ -1098,11 +1098,21 @@ int pbvd_decode_packed_pm8(pbvd_ctx* c, const uint32_t* d_words, int q, size_t n
   if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
   if (c->P != 0 || c->mode != 0) return PBVD_EUNSUPPORTED;
   pbvd::Pm8Plan plan;
-  if (pbvd::pm8_plan(c->K, c->R, c->gens, q, &plan) != 0) return PBVD_EUNSUPPORTED;
   int64_t I = 0, nquads = 0;
   size_t in_words = 0, surv_words = 0;
   pbvd::pm8_sizes(c->K, c->R, (int64_t)n_stages, c->D, c->L, &I, &nquads, &in_words, &surv_words);
-  if ((nquads + 31) / 32 > INT32_MAX) return PBVD_EINVAL;
+  // threads per four blocks: 1 or 2 when the context's threads_per_pair says
+  // so; otherwise two (where built) while one thread per four blocks would
+  // leave fewer than two warps per SM (measured: 2^24-bit K=7 stream at
+  // D = 512, 8,193 quads: 0.55 against 0.84 ms; at D = 256: 0.57 against
+  // 0.50 ms)
+  int lanes = c->cfg.threads_per_pair;
+  if (lanes != 1 && lanes != 2) {
+    pbvd::Pm8Plan two;
+    lanes = (nquads < (int64_t)64 * c->sm_count && pbvd::pm8_plan(c->K, c->R, c->gens, q, 2, &two) == 0) ? 2 : 1;
+  }
+  if (pbvd::pm8_plan(c->K, c->R, c->gens, q, lanes, &plan) != 0) return PBVD_EUNSUPPORTED;
+  if ((2 * nquads + 31) / 32 > INT32_MAX) return PBVD_EINVAL;
   int rc = grow_device(&c->pm8_in, &c->pm8_in_cap, in_words * 4);
   if (rc != PBVD_OK) return rc;
   rc = grow_device(&c->pm8_surv, &c->pm8_surv_cap, surv_words * 4);

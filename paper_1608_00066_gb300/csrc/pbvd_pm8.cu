@@ -133,7 +133,8 @@ __host__ __device__ __forceinline__ Pm8Pb pm8_pb(const Pm8Args& a, int64_t b) {
 // The biased values a = lambda + Q (lambda clamped at -Q) of the four blocks
 // of a quad, one word per stage and code bit; a = Q (lambda = 0, the same
 // metric for every codeword) past a block's end.  Thread: one quad, 32
-// stages.
+// stages; each block's values are read in order, the word and the position
+// in it advanced value by value.
 template <int Q_BITS>
 __global__ void __launch_bounds__(256) pm8_gather_kernel(const uint32_t* __restrict__ words, const Pm8Args a, int R,
                                                          uint32_t* __restrict__ in) {
@@ -141,21 +142,29 @@ __global__ void __launch_bounds__(256) pm8_gather_kernel(const uint32_t* __restr
   constexpr int QM = Q_BITS == 1 ? 1 : (1 << (Q_BITS - 1)) - 1;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nquads) return;
-  Pm8Pb pb[4];
-#pragma unroll
-  for (int l = 0; l < 4; ++l) pb[l] = pm8_pb(a, 4 * q + l);
   const int i0 = blockIdx.y * 32;
   const int i1 = i0 + 32 < a.I ? i0 + 32 : a.I;
+  int len[4];
+  int64_t wi[4];   // word holding the block's next value
+  int slot[4];     // position of that value in the word
+  uint32_t cur[4]; // that word
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const Pm8Pb p = pm8_pb(a, 4 * q + l);
+    len[l] = p.len;
+    const int64_t idx = (p.f0 + i0) * R;
+    wi[l] = idx / M;
+    slot[l] = (int)(idx - wi[l] * M);
+    cur[l] = i0 < p.len ? __ldg(words + wi[l]) : 0u;
+  }
   for (int i = i0; i < i1; ++i) {
     for (int r = 0; r < R; ++r) {
       uint32_t acc = 0;
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         int val = QM;
-        if (i < pb[l].len) {
-          const int64_t idx = (pb[l].f0 + i) * R + r;
-          const uint32_t w = __ldg(words + idx / M);
-          const uint32_t u = (w >> (Q_BITS * (int)(idx % M))) & ((1u << Q_BITS) - 1u);
+        if (i < len[l]) {
+          const uint32_t u = (cur[l] >> (Q_BITS * slot[l])) & ((1u << Q_BITS) - 1u);
           int lam;
           if (Q_BITS == 1) {
             lam = u ? -1 : 1;
@@ -164,6 +173,13 @@ __global__ void __launch_bounds__(256) pm8_gather_kernel(const uint32_t* __restr
             lam = lam < -QM ? -QM : lam;
           }
           val = lam + QM;
+          if (++slot[l] == M) {
+            slot[l] = 0;
+            ++wi[l];
+            // the next word, if the block has a value left in it
+            const int64_t left = (int64_t)(len[l] - i) * R - r - 1;
+            if (left > 0) cur[l] = __ldg(words + wi[l]);
+          }
         }
         acc |= (uint32_t)val << (8 * l);
       }
@@ -354,6 +370,203 @@ __global__ void __launch_bounds__(32) pm8_decode_kernel(const Pm8Args a) {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// Two lanes per quad (64-state codes): lane h holds the states h N/2 ..
+// h N/2 + N/2 - 1 of the four blocks (local index k = state - h N/2).  Lane
+// h's butterfly jl (jl < N/4) joins its local predecessors 2 jl, 2 jl + 1
+// (the states 2 j', 2 j' + 1 with j' = jl + h N/4) into the successors j'
+// (lower, lane 0's local j') and j' + N/2 (upper, lane 1's local j'): lane 0
+// keeps its lower successors and hands the upper ones to lane 1, lane 1 keeps
+// its upper successors and hands the lower ones to lane 0, one shfl.xor per
+// butterfly.  Lane 1's codewords are lane 0's xor the taps of the top state
+// bit, so each lane relabels its 2^R branch metrics once per stage and the
+// butterfly code is the same in both lanes.  The traceback splits the four
+// chains over the two lanes.
+template <class C, int RKS>
+__global__ void __launch_bounds__(32) pm8_decode2_kernel(const Pm8Args a) {
+  constexpr int v = C::v, N = C::N, H = C::H, R = C::R, W = C::W;
+  constexpr int NL = N / 2, NB = N / 4;  // states and butterflies per lane
+  constexpr int NCW = 1 << R;
+  constexpr int CS = 8, RB = 4;
+  constexpr uint32_t TOP = C::cw(NL, 0);  // codeword taps of state bit v - 1
+  static_assert(v % RKS == 0, "renormalisation interval divides the period");
+  static_assert(NB % 8 == 0, "whole survivor words per lane");
+  extern __shared__ __align__(16) uint32_t pm8_ring[];
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t q = gt >> 1;
+  const int h = (int)(gt & 1);
+  if (q >= a.nquads) return;  // both lanes of a quad leave together
+  const unsigned pmask = 3u << (threadIdx.x & 30);
+  const uint32_t hm = h ? 0xFFFFFFFFu : 0u;
+  Pm8Pb pb[4];
+  uint32_t kmask = 0;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    pb[l] = pm8_pb(a, 4 * q + l);
+    if (pb[l].len > 0 && pb[l].f0 == 0) kmask |= 0xFFu << (8 * l);
+  }
+  uint32_t pm[NL];
+#pragma unroll
+  for (int k = 0; k < NL; ++k) pm[k] = a.big4 & kmask;
+  pm[0] &= hm;  // S_0 (lane 0, local 0) starts at 0
+
+  const int64_t in_stride = a.nquads * R, sv_stride = a.nquads * W;
+  const uint32_t* inp = a.in + q * R;
+  uint32_t* svp = a.surv + q * W;
+  int per = 0;
+  for (int i0 = 0; i0 < a.I; i0 += v) {
+    uint32_t x[v][R];
+#pragma unroll
+    for (int p = 0; p < v; ++p)
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[p][r] = (i0 + p < a.I) ? __ldg(inp + (int64_t)(i0 + p) * in_stride + r) : 0u;
+#pragma unroll
+    for (int p = 0; p < v; ++p) {
+      if (i0 + p >= a.I) break;
+      uint32_t cmp[R], bm[NCW], bl[NCW];
+#pragma unroll
+      for (int r = 0; r < R; ++r) cmp[r] = a.twoq4 - x[p][r];
+#pragma unroll
+      for (int c = 0; c < NCW; ++c) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) t += ((c >> (R - 1 - r)) & 1) ? x[p][r] : cmp[r];
+        bm[c] = t;
+      }
+#pragma unroll
+      for (int c = 0; c < NCW; ++c) bl[c] = h ? bm[c ^ TOP] : bm[c];
+      uint32_t nw[NL], mlo[NB], mhi[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const uint32_t u0 = pm[2 * j], u1 = pm[2 * j + 1];
+        uint32_t o[2];
+#pragma unroll
+        for (int xb = 0; xb < 2; ++xb) {
+          const uint32_t c0 = u0 + bl[C::cw(2 * j, xb)];
+          const uint32_t c1 = u1 + bl[C::cw(2 * j + 1, xb)];
+          const uint32_t m = sign_mask(c1 + kByteSign - c0);
+          o[xb] = (c0 & m) | (c1 & ~m);
+          if (xb) mhi[j] = m; else mlo[j] = m;
+        }
+        const uint32_t send = (o[0] & hm) | (o[1] & ~hm);
+        const uint32_t got = __shfl_xor_sync(pmask, send, 1);
+        nw[j] = (got & hm) | (o[0] & ~hm);
+        nw[j + NB] = (o[1] & hm) | (got & ~hm);
+      }
+      if (i0 == 0 && kmask) {
+#pragma unroll
+        for (int k = 0; k < NL; ++k)
+          if (k & ((1 << (v - p - 1)) - 1)) nw[k] = (nw[k] & ~kmask) | (a.big4 & kmask);
+      }
+      uint32_t rl[NB / 8], rh[NB / 8];
+#pragma unroll
+      for (int w = 0; w < NB / 8; ++w) {
+        rl[w] = merge_masks<0, 8>(mlo + 8 * w);
+        rh[w] = merge_masks<0, 8>(mhi + 8 * w);
+      }
+      // lower successors h N/4 + jl: words h NB/8 ..; upper: (H + h NB)/8 ..
+      uint32_t* dst = svp + (int64_t)(i0 + p) * sv_stride;
+#pragma unroll
+      for (int w = 0; w < NB / 8; w += 2) {
+        *reinterpret_cast<uint2*>(dst + h * (NB / 8) + w) = make_uint2(rl[w], rl[w + 1]);
+        *reinterpret_cast<uint2*>(dst + (H + h * NB) / 8 + w) = make_uint2(rh[w], rh[w + 1]);
+      }
+#pragma unroll
+      for (int k = 0; k < NL; ++k) pm[k] = nw[k];
+      bool rn;
+      if constexpr (RKS < v) {
+        rn = (p + 1) % RKS == 0;
+      } else {
+        rn = false;
+        if (p == v - 1 && ++per == a.rp) {
+          per = 0;
+          rn = true;
+        }
+      }
+      if (rn) {
+        uint32_t t[NL / 2];
+#pragma unroll
+        for (int j = 0; j < NL / 2; ++j) t[j] = byte_min(pm[2 * j], pm[2 * j + 1]);
+#pragma unroll
+        for (int w = NL / 4; w >= 1; w /= 2)
+#pragma unroll
+          for (int j = 0; j < w; ++j) t[j] = byte_min(t[2 * j], t[2 * j + 1]);
+        const uint32_t mn = byte_min(t[0], __shfl_xor_sync(pmask, t[0], 1));
+#pragma unroll
+        for (int k = 0; k < NL; ++k) pm[k] -= mn;
+      }
+    }
+  }
+
+  // traceback: lane h walks the chains of blocks 2h and 2h + 1
+  Pm8Pb cb[2];
+  cb[0] = h ? pb[2] : pb[0];
+  cb[1] = h ? pb[3] : pb[1];
+  int imin = a.I;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    if (cb[c].len > 0 && cb[c].ob < imin) imin = cb[c].ob;
+  if (imin >= a.I) return;  // neither block exists
+  uint32_t* ring = pm8_ring + threadIdx.x * (RB * CS * W);
+  const int top = a.I - 1;
+  const int ctop = top / CS, cbot = imin / CS;
+  auto issue = [&](int c) {
+    if (c >= cbot) {
+      uint32_t* slot = ring + (c % RB) * (CS * W);
+#pragma unroll
+      for (int k = 0; k < CS; ++k) {
+        const int i = c * CS + k;
+        if (i <= top) {
+          const uint32_t* src = a.surv + ((int64_t)i * a.nquads + q) * W;
+          const uint32_t d = (uint32_t)__cvta_generic_to_shared(slot + k * W);
+#pragma unroll
+          for (int w = 0; w < W; w += 4)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 4 * w), "l"(src + w));
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  for (int k = 0; k < RB - 1; ++k) issue(ctop - k);
+  int st[2] = {0, 0};
+  uint32_t acc[2] = {0, 0};
+  const int sh0 = 16 * h;  // bit offset of block 2h in a record word
+  for (int c = ctop; c >= cbot; --c) {
+    issue(c - (RB - 1));
+    asm volatile("cp.async.wait_group %0;" ::"n"(RB - 1) : "memory");
+    const uint32_t* slot = ring + (c % RB) * (CS * W);
+    const int ihi = top < c * CS + CS - 1 ? top : c * CS + CS - 1;
+    const int ilo = imin > c * CS ? imin : c * CS;
+    for (int i = ihi; i >= ilo; --i) {
+      const uint32_t* rec = slot + (i - c * CS) * W;
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        if (i < cb[cc].len) {
+          if (i >= cb[cc].ob && i < cb[cc].oe) {
+            const int64_t S = cb[cc].f0 + i;
+            acc[cc] |= (uint32_t)((st[cc] >> (v - 1)) & 1) << (S & 7);
+            if ((S & 7) == 0) {
+              a.out[S >> 3] = (uint8_t)acc[cc];
+              acc[cc] = 0;
+            }
+          }
+          const uint32_t up = (rec[st[cc] >> 3] >> (sh0 + 8 * cc + (st[cc] & 7))) & 1u;
+          st[cc] = ((st[cc] & (H - 1)) << 1) | (int)(up ^ 1u);
+        }
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <class C, int RKS>
+cudaError_t pm8_run2(const Pm8Args& a, cudaStream_t s) {
+  constexpr int cta = 32;
+  const int64_t grid = (2 * a.nquads + cta - 1) / cta;
+  const size_t smem = (size_t)cta * 4 * 8 * C::W * sizeof(uint32_t);
+  pm8_decode2_kernel<C, RKS><<<(unsigned)grid, cta, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class C, int RKS>
 cudaError_t pm8_run(const Pm8Args& a, cudaStream_t s) {
   constexpr int cta = 32;
@@ -371,20 +584,25 @@ struct Pm8Inst {
   int K, R;
   uint32_t g[3];
   int rks;
+  int lanes;  // threads per quad
   cudaError_t (*run)(const Pm8Args&, cudaStream_t);
 };
 
 const Pm8Inst kPm8[] = {
-    {7, 2, {0171u, 0133u, 0u}, 3, &pm8_run<P7, 3>},
-    {7, 2, {0171u, 0133u, 0u}, 6, &pm8_run<P7, 6>},
-    {7, 3, {0171u, 0165u, 0133u}, 1, &pm8_run<P7R3, 1>},
-    {7, 3, {0171u, 0165u, 0133u}, 6, &pm8_run<P7R3, 6>},
-    {5, 2, {023u, 035u, 0u}, 4, &pm8_run<P5, 4>},
+    {7, 2, {0171u, 0133u, 0u}, 3, 1, &pm8_run<P7, 3>},
+    {7, 2, {0171u, 0133u, 0u}, 6, 1, &pm8_run<P7, 6>},
+    {7, 2, {0171u, 0133u, 0u}, 3, 2, &pm8_run2<P7, 3>},
+    {7, 2, {0171u, 0133u, 0u}, 6, 2, &pm8_run2<P7, 6>},
+    {7, 3, {0171u, 0165u, 0133u}, 1, 1, &pm8_run<P7R3, 1>},
+    {7, 3, {0171u, 0165u, 0133u}, 6, 1, &pm8_run<P7R3, 6>},
+    {7, 3, {0171u, 0165u, 0133u}, 1, 2, &pm8_run2<P7R3, 1>},
+    {7, 3, {0171u, 0165u, 0133u}, 6, 2, &pm8_run2<P7R3, 6>},
+    {5, 2, {023u, 035u, 0u}, 4, 1, &pm8_run<P5, 4>},
 };
 
 }  // namespace
 
-int pm8_plan(int K, int R, const uint32_t* gens, int q, Pm8Plan* p) {
+int pm8_plan(int K, int R, const uint32_t* gens, int q, int lanes, Pm8Plan* p) {
   if (q < 1 || q > 8) return -1;
   const int Q = q == 1 ? 1 : (1 << (q - 1)) - 1;
   const int bmmax = 2 * Q * R;
@@ -399,7 +617,9 @@ int pm8_plan(int K, int R, const uint32_t* gens, int q, Pm8Plan* p) {
     for (int r = 0; r < R; ++r) same = same && e.g[r] == gens[r];
     if (!same) continue;
     const bool fits = e.rks < v ? e.rks <= k : k >= v;
-    if (fits && (best < 0 || e.rks > kPm8[best].rks)) best = i;
+    if (!fits || (lanes > 0 && e.lanes != lanes)) continue;
+    // the longest renormalisation interval, then the most lanes
+    if (best < 0 || e.rks > kPm8[best].rks || (e.rks == kPm8[best].rks && e.lanes > kPm8[best].lanes)) best = i;
   }
   if (best < 0) return -1;
   p->inst = best;
@@ -408,6 +628,7 @@ int pm8_plan(int K, int R, const uint32_t* gens, int q, Pm8Plan* p) {
   p->bmmax = bmmax;
   p->rks = kPm8[best].rks;
   p->rp = kPm8[best].rks == v ? k / v : 1;
+  p->lanes = kPm8[best].lanes;
   return 0;
 }
 

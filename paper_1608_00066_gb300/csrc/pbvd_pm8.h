@@ -8,16 +8,18 @@
 namespace pbvd {
 
 // The kernel instance and renormalisation interval for code (K, R, gens) on
-// q-bit values: pm8_plan returns -1 when no instance is built for the code or
-// when K * 2QR >= 127 (the metrics would not fit in bytes).
+// q-bit values with `lanes` threads per four blocks (0: the most built):
+// pm8_plan returns -1 when no such instance is built or when K * 2QR >= 127
+// (the metrics would not fit in bytes).
 struct Pm8Plan {
   int inst;   // index of the kernel instance
   int q, Q;
   int bmmax;  // 2QR
   int rks;    // stages between renormalisations (K - 1: every rp periods)
   int rp;
+  int lanes;  // threads per four blocks
 };
-int pm8_plan(int K, int R, const uint32_t* gens, int q, Pm8Plan* p);
+int pm8_plan(int K, int R, const uint32_t* gens, int q, int lanes, Pm8Plan* p);
 
 // Lock-step stages I, quads of blocks, and the words of the gathered values
 // and of the survivor records of a stream of n stages.

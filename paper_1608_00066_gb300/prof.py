@@ -8,6 +8,7 @@ pointed at a known launch (skip the warm-up launches, capture the next).
     python -m paper_1608_00066_gb300.prof stream ...
     python -m paper_1608_00066_gb300.prof frame  [--tune JSON] ...
     python -m paper_1608_00066_gb300.prof two    ...
+    python -m paper_1608_00066_gb300.prof pm8    [--q Q] [--D D] ...
 
 Workloads (the benchmark's):
   k7     K=7 r1/2 (171,133) terminated stream, 2^24 info bits, 3 dB, D=512 L=42
@@ -16,6 +17,9 @@ Workloads (the benchmark's):
   stream 64 continuous K7 r1/2 streams, 4096 stages per push, one launch per push
   frame  one K7 r1/2 frame of 4096 info bits, 3 dB, D=512 L=42 (latency case)
   two    the k7 stream with the paper's two-kernel design (K1 then K2 per call)
+  pm8    the k7 stream as packed q-bit words (default q = 3), 8-bit path
+         metrics (gather kernel, then one thread per four blocks); D = 512
+         unless --D is given
 
 Prints one line per launch set: the workload, the configuration and the mean
 device time per launch (CUDA events; L2 not flushed, so do not use it as a
@@ -69,6 +73,17 @@ def run_two_kernel(torch, warmup, reps):
     return ms, {"design": "two-kernel (K1 + K2)"}
 
 
+def run_pm8(torch, q, D, warmup, reps):
+    spec = synth.K7_R12
+    f = synth.make_packed_frame(spec, 1 << 24, 3.0, q, seed=2003)
+    dec = pbvd.Decoder(spec.K, spec.gens, None, D, 42)
+    w = torch.from_numpy(f.words.view(np.int32).copy()).cuda()
+    out = torch.empty((f.n_stages + 7) // 8, dtype=torch.uint8, device="cuda")
+    ms = _events(torch, lambda: dec.decode_packed_pm8(w, q, f.n_stages, out), warmup, reps)
+    dec.close()
+    return ms, {"q": q, "D": D, "L": 42, "path_metrics": "8-bit, four blocks per register"}
+
+
 def run_batch(torch, warmup, reps):
     from . import tune as tn
     frames = synth.batch_frames(10000, seed=4001)
@@ -111,10 +126,12 @@ def run_streams(torch, warmup, reps, n_streams=64, chunk=4096):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("target", choices=["k7", "k9", "batch", "stream", "frame", "two"])
+    ap.add_argument("target", choices=["k7", "k9", "batch", "stream", "frame", "two", "pm8"])
     ap.add_argument("--tune", default="", help="JSON kernel configuration for k7 / k9")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--q", type=int, default=3, help="bits per soft value (pm8)")
+    ap.add_argument("--D", type=int, default=512, help="block length (pm8)")
     args = ap.parse_args(argv)
     import torch
     build.build()
@@ -127,6 +144,8 @@ def main(argv=None):
         ms, cfg = run_stream_decode(torch, synth.K7_R12, 4096, 3.0, 1001, 512, 42, tune, args.warmup, args.reps)
     elif args.target == "two":
         ms, cfg = run_two_kernel(torch, args.warmup, args.reps)
+    elif args.target == "pm8":
+        ms, cfg = run_pm8(torch, args.q, args.D, args.warmup, args.reps)
     elif args.target == "batch":
         ms, cfg = run_batch(torch, args.warmup, args.reps)
     else:

@@ -39,6 +39,11 @@ def _bits(out, n):
     return np.unpackbits(out.cpu().numpy(), bitorder="little")[:n]
 
 
+def _lanes(spec):
+    """Threads per four blocks built for the code (two only for 64 states)."""
+    return (1, 2) if spec.K == 7 else (1,)
+
+
 @pytest.mark.parametrize("q", [1, 2, 3])
 @pytest.mark.parametrize("name", list(CODES))
 def test_pm8_matches_oracle(name, q):
@@ -48,11 +53,13 @@ def test_pm8_matches_oracle(name, q):
         for k, eb in ((5000, 1.0), (777, 0.0), (1, 2.0)):
             f = synth.make_packed_frame(spec, k, eb, q, seed=k * 7 + q + D)
             want = _want(spec, q, f.words, f.n_stages, D, L)
-            out = dec.decode_packed_pm8(_words(f), q, f.n_stages)
-            torch.cuda.synchronize()
-            got = _bits(out, f.n_stages)
-            bad = np.flatnonzero(got != want)
-            assert bad.size == 0, (name, q, D, L, k, bad[:8])
+            for lanes in _lanes(spec):
+                dec.set_config(threads_per_pair=lanes)
+                out = dec.decode_packed_pm8(_words(f), q, f.n_stages)
+                torch.cuda.synchronize()
+                got = _bits(out, f.n_stages)
+                bad = np.flatnonzero(got != want)
+                assert bad.size == 0, (name, q, D, L, k, lanes, bad[:8])
         dec.close()
 
 
@@ -60,7 +67,7 @@ def test_pm8_matches_oracle(name, q):
 def test_pm8_random_words(q):
     """Words of uniformly random bits: every q-bit code equally likely (for
     q >= 2 the value -Q-1 too, read as -Q), metrics as spread as noise makes
-    them; several ragged lengths."""
+    them; several ragged lengths, one and two threads per four blocks."""
     spec = synth.K7_R12
     rng = np.random.default_rng(100 + q)
     dec = pbvd.Decoder(spec.K, spec.gens, None, 256, 42)
@@ -68,9 +75,11 @@ def test_pm8_random_words(q):
     for n in (9, 300, 4099, 70001):
         words = rng.integers(0, 1 << 32, size=(n * 2 + m - 1) // m, dtype=np.uint64).astype(np.uint32)
         want = _want(spec, q, words, n, 256, 42)
-        out = dec.decode_packed_pm8(torch.from_numpy(words.view(np.int32)).cuda(), q, n)
-        torch.cuda.synchronize()
-        assert np.array_equal(_bits(out, n), want), (q, n)
+        for lanes in (1, 2):
+            dec.set_config(threads_per_pair=lanes)
+            out = dec.decode_packed_pm8(torch.from_numpy(words.view(np.int32)).cuda(), q, n)
+            torch.cuda.synchronize()
+            assert np.array_equal(_bits(out, n), want), (q, n, lanes)
     dec.close()
 
 
@@ -84,10 +93,14 @@ def test_pm8_equals_16bit_path_full_stream(q):
     n = f.n_stages
     dec = pbvd.Decoder(spec.K, spec.gens, None, 512, 42)
     w = _words(f)
-    got = _bits(dec.decode_packed_pm8(w, q, n), n)
     ref = _bits(dec.decode_packed(w, q, n), n)
+    dec.set_config(threads_per_pair=1)
+    one = _bits(dec.decode_packed_pm8(w, q, n), n)
+    dec.set_config(threads_per_pair=0)
+    got = _bits(dec.decode_packed_pm8(w, q, n), n)
     torch.cuda.synchronize()
     assert np.array_equal(got, ref)
+    assert np.array_equal(one, ref)
     pre = 1 << 18
     want = oracle.viterbi_block_q(7, spec.gens, oracle.unpack_soft(q, f.words, pre * 2).reshape(pre, 2), 512, 42,
                                   oracle.q_max(q))
