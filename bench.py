@@ -101,11 +101,25 @@ def peak_int16_ops(sm_count: int = 152, clock_hz: float = 2.07e9) -> float:
     return sm_count * 4 * 32 * 2 * clock_hz
 
 
-def peak_source(sm_count: int, mhz: float) -> str:
-    return ("issue limit: %d SMs (device) x 4 schedulers x 32 lanes x 2 (16x2) x %.0f MHz (the SM clock's "
-            "maximum as sampled); the ALU pipe alone issues half of that (64 lanes/clk/SM, measured), "
-            "and the kernels place part of their adds on the FMA pipe, so the issue limit is the "
-            "ceiling" % (sm_count, mhz))
+def peak_source(sm_count: int, mhz: float, rates=None) -> str:
+    txt = ("issue limit: %d SMs (device) x 4 schedulers x 32 lanes x 2 (16x2) x %.0f MHz (the SM clock's "
+           "maximum as sampled); the ALU pipe alone issues half of that, and the kernels place part of their "
+           "adds on the FMA pipe, so the issue limit is the ceiling" % (sm_count, mhz))
+    if rates and "lop3" in rates:
+        txt += ("; measured on this device (pbvd_measure_int_rate, thread operations per clock per SM): "
+                "lop3 %.1f, imad %.1f, lop3+imad %.1f, 16x2 add-min %.1f" %
+                (rates["lop3"], rates["imad"], rates["lop3+imad"], rates["viaddmnmx_s16x2"]))
+    return txt
+
+
+def measure_int_rates() -> dict:
+    """Thread operations per clock per SM of the decode kernels' instruction
+    kinds on this device (pbvd_measure_int_rate; after the timed regions)."""
+    from paper_1608_00066_gb300 import pbvd
+    try:
+        return {name: round(pbvd.pbvd_measure_int_rate(op), 1) for op, name in pbvd.INT_RATE_OPS.items()}
+    except Exception as e:  # the benchmark line still prints; the failure is recorded in it
+        return {"error": str(e)}
 
 
 # ------------------------------------------------------------------ clocks
@@ -424,6 +438,7 @@ def run_ours(args, rank: int, world: int):
     ops = algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP) * K_INFO
     clocks = clk.summary()
     sms = device_sm_count()
+    rates = measure_int_rates() if rank == 0 else None
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = peak_int16_ops(sms, max_mhz * 1e6)
     achieved = ops / (ms * 1e-3)
@@ -443,7 +458,8 @@ def run_ours(args, rank: int, world: int):
                      "unit": "Tops/s (int16)", "frac": round(achieved / peak, 4),
                      "ops_per_bit": round(algorithmic_ops_per_bit(64, D_BLOCK, L_OVERLAP), 2),
                      "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "peak_source": peak_source(sms, max_mhz),
+                     "peak_source": peak_source(sms, max_mhz, rates),
+                     "measured_ops_per_clk_per_sm": rates,
                      "kernel_sources": kernel_sources_hash()},
         "roofline_hbm": {"bound": "hbm", "achieved": round(alg_bytes / (ms * 1e-3) / 1e9, 1),
                          "peak": hbm_peak, "unit": "GB/s", "frac": round(alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 4),

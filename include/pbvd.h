@@ -382,6 +382,18 @@ PBVD_API int64_t pbvd_stream_released(const pbvd_stream *s);
 /* Frees the stream's device state (synchronises the device first). */
 PBVD_API void pbvd_stream_destroy(pbvd_stream *s);
 
+/* Measurement helper, not a decoding call: the integer issue rate of the
+ * current device for one kind of instruction the decode kernels are built
+ * from, in thread-level operations per clock per SM (a 16x2 operation counts
+ * once).  op: 0 the 16x2 DPX add-min, 1 a three-input add, 2 a three-input
+ * logic op, 3 a byte permute, 4 an integer multiply-add (FMA pipe), 5 logic
+ * op and multiply-add interleaved, 6 16x2 add-min and multiply-add
+ * interleaved.  Eight independent chains per thread, 2,048 threads per SM,
+ * SM cycles from clock64; runs for a few milliseconds on the legacy default
+ * stream and synchronises the device.  PBVD_EINVAL for another op,
+ * PBVD_ENOMEM, PBVD_ECUDA. */
+PBVD_API int pbvd_measure_int_rate(int op, double *ops_per_clk_per_sm);
+
 /* Message for an error code (static string). */
 PBVD_API const char *pbvd_strerror(int code);
 

@@ -28,7 +28,7 @@ __device__ __forceinline__ void run_tile(const KArgs& a, const BatchArgs& b, con
   wk.hasB = p.hasB != 0;
   constexpr int SW = scratch_words_per_group<C, T>();
   const int64_t slot = (int64_t)blockIdx.x * b.gmax + g;
-  decode_pair<C, T, PUNCT, false>(a, wk, slot, smem + g * SW, nullptr);
+  decode_pair<C, T, PUNCT, false, false, false>(a, wk, slot, smem + g * SW, nullptr);
 }
 
 template <class C0, int T0, bool P0, class C1, int T1, bool P1, class C2, int T2, bool P2>

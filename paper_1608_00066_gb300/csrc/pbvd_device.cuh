@@ -976,8 +976,10 @@ __device__ __forceinline__ void tb_walk_any(const KArgs& a, int64_t gslot, const
 }
 
 // start[x]: physical index of the state PB x's traceback starts from at its
-// last forward stage (0 = S_0, whose index is 0 in every layout).
-template <class C, int T, bool SMEM>
+// last forward stage (0 = S_0, whose index is 0 in every layout).  PAR: walk
+// failed guesses again side by side before the top-down check (the batch
+// kernels leave it out: in their register budget it costs spills).
+template <class C, int T, bool SMEM, bool PAR = true>
 __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, const PbRun& gB, bool hasB, int J,
                                                int64_t gslot, uint32_t* scratch, const uint32_t* svs,
                                                const int (&start)[2]) {
@@ -1046,7 +1048,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     // lanes.  The exit of a segment above is exact unless that segment was
     // itself walked again and ended elsewhere, which the top-down check below
     // finds (and walks again, one segment after another) as before.
-    for (int pb = 0; pb < (hasB ? 2 : 1); ++pb) {
+    for (int pb = 0; pb < (PAR ? (hasB ? 2 : 1) : 0); ++pb) {
       const PbRun& gp = pb ? gB : gA;
       const int jend_p = pb ? jB : jA;
       const int seg_p = BOTH ? seg : (((jend_p + 1 + SPB - 1) / SPB) + 7) & ~7;
@@ -1106,7 +1108,8 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
 
 // VAR: honour the traceback and frame variants of KArgs (argmin start state,
 // tail-biting windows); the batch kernel decodes the plain scheme only.
-template <class C, int T, bool PUNCT, bool SMEM, bool VAR = false>
+// PAR: see traceback_pair.
+template <class C, int T, bool PUNCT, bool SMEM, bool VAR = false, bool PAR = true>
 __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, int64_t gslot,
                                             uint32_t* __restrict__ scratch, uint32_t* __restrict__ svs) {
   using S = Shape<C, T>;
@@ -1243,7 +1246,7 @@ __device__ __forceinline__ void decode_pair(const KArgs& a, const PairWork& wk, 
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 
-  traceback_pair<C, T, SMEM>(a, gA, gB, wk.hasB, J, gslot, scratch, svs, start);
+  traceback_pair<C, T, SMEM, PAR>(a, gA, gB, wk.hasB, J, gslot, scratch, svs, start);
 }
 
 // Minimum resident CTAs of 256 threads the compiler is asked to allow: 2 (at
@@ -1260,7 +1263,10 @@ __host__ __device__ constexpr int decode_min_ctas() {
 // survivor records of each group in shared memory (a.smem_rec_words words
 // per group), else in a.surv.
 // VAR: the instance honours the variants of KArgs (argmin traceback start,
-// tail-biting windows); the plain instances carry none of that code.
+// tail-biting windows); the plain instances carry none of that code.  The
+// traceback's parallel re-walk round is left out where the launch bounds
+// hold the kernel to 128 registers (it spilled there and cost 4.5 % of the
+// K=9 stream at eight threads per pair).
 template <class C, int T, bool PUNCT, bool SMEM, bool VAR = false>
 __global__ void __launch_bounds__(256, decode_min_ctas<C, T>()) pbvd_decode_kernel(const KArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -1280,7 +1286,7 @@ __global__ void __launch_bounds__(256, decode_min_ctas<C, T>()) pbvd_decode_kern
   wk.B = wk.A;
   wk.B.b = wk.A.b + 1;
   wk.hasB = wk.B.b < a.n_blocks;
-  decode_pair<C, T, PUNCT, SMEM, VAR>(a, wk, pair, scratch, svs);
+  decode_pair<C, T, PUNCT, SMEM, VAR, decode_min_ctas<C, T>() == 1>(a, wk, pair, scratch, svs);
 }
 
 }  // namespace pbvd

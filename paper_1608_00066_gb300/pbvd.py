@@ -37,7 +37,7 @@ EXPORTS = (
     "pbvd_stream_open", "pbvd_stream_push", "pbvd_stream_push_many", "pbvd_stream_close",
     "pbvd_stream_released", "pbvd_stream_destroy", "pbvd_batch_update", "pbvd_decode_host",
     "pbvd_decode_packed", "pbvd_decode_host_packed", "pbvd_set_mode", "pbvd_get_mode",
-    "pbvd_decode_two_kernel", "pbvd_decode_packed_pm8",
+    "pbvd_decode_two_kernel", "pbvd_decode_packed_pm8", "pbvd_measure_int_rate",
 )
 
 PBVD_MODE_ARGMIN = 1
@@ -102,6 +102,8 @@ def load(path: Optional[str] = None):
         lib.pbvd_decode_packed.restype = I
         lib.pbvd_decode_packed_pm8.argtypes = [V, V, I, SZ, V, V]
         lib.pbvd_decode_packed_pm8.restype = I
+        lib.pbvd_measure_int_rate.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
+        lib.pbvd_measure_int_rate.restype = I
         lib.pbvd_decode_host_packed.argtypes = [V, V, I, SZ, V, I, V]
         lib.pbvd_decode_host_packed.restype = I
         lib.pbvd_llr_count.argtypes = [V, SZ, ctypes.POINTER(SZ)]
@@ -217,6 +219,18 @@ def pbvd_decode_packed_pm8(ctx: int, d_words: int, q: int, n_stages: int, d_out:
     (device pointers; small q only, PBVD_EUNSUPPORTED otherwise)."""
     _check(load().pbvd_decode_packed_pm8(ctx, d_words, q, n_stages, d_out, stream or None),
            "pbvd_decode_packed_pm8")
+
+
+INT_RATE_OPS = {0: "viaddmnmx_s16x2", 1: "add3", 2: "lop3", 3: "prmt", 4: "imad", 5: "lop3+imad",
+                6: "viaddmnmx+imad"}
+
+
+def pbvd_measure_int_rate(op: int) -> float:
+    """Thread-level operations per clock per SM of one instruction kind on the
+    current device (see INT_RATE_OPS); a measurement helper."""
+    r = ctypes.c_double()
+    _check(load().pbvd_measure_int_rate(op, ctypes.byref(r)), "pbvd_measure_int_rate")
+    return float(r.value)
 
 
 def pbvd_decode_host_packed(ctx: int, h_words: int, q: int, n_stages: int, h_out: int, segments: int = 0,
