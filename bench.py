@@ -78,7 +78,7 @@ def profiled_traffic(key):
 
 
 def hbm_peak_gbs() -> tuple:
-    """Measured copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else
+    """Measured copy bandwidth of this kind of GPU (MEASURED_PEAKS.json), else
     the fallback figure."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
