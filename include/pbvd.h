@@ -204,7 +204,8 @@ PBVD_API int pbvd_decode_packed(pbvd_ctx *ctx, const uint32_t *d_words, int q, s
  * copy pipeline moves the packed words host -> device, unpacks each run's
  * values on the device as soon as its words have arrived, and decodes the
  * runs as pbvd_decode_host does.  segments >= 0 (direct access is not
- * offered for packed input). */
+ * offered for packed input); segments = 0 picks up to 2 runs for q <= 3 and
+ * up to 4 for larger q. */
 PBVD_API int pbvd_decode_host_packed(pbvd_ctx *ctx, const uint32_t *h_words, int q, size_t n_stages,
                                      uint8_t *h_out, int segments, void *stream);
 

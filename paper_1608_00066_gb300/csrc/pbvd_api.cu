@@ -951,13 +951,17 @@ int decode_host_impl(pbvd_ctx* c, const void* h_in, int q, size_t n_stages, uint
   int rc = plan_decode(&cc, n_stages, &p);
   if (rc != PBVD_OK) return rc;
   const int64_t nb = p.n_blocks;
-  // runs of whole pairs of blocks; automatic: up to 6 runs of at least 1024
-  // blocks.  A run's decode takes at least the dependency chain of one pair
+  // runs of whole pairs of blocks; automatic: up to 6 runs (fewer for packed
+  // input, below) of at least 1024 blocks.  A run's decode takes at least the dependency chain of one pair
   // (about half the whole stream's decode time for 4 threads per pair), so
   // more, shorter runs start sooner but end no sooner; runs with a
   // different kernel configuration (a shorter chain) slowed the whole call
   // down, the kernels sharing the SMs badly.
-  int64_t want = segments > 0 ? segments : std::max<int64_t>(1, std::min<int64_t>(6, nb / 1024));
+  // Packed input crosses the link in a fraction of the time, and its runs
+  // also wait for their unpacking: fewer runs (measured on the 2^24-bit K=7
+  // stream: 2 runs best for q <= 3, 4 for q >= 4, against 6 for int8 input).
+  const int64_t auto_runs = q == 0 ? 6 : (q <= 3 ? 2 : 4);
+  int64_t want = segments > 0 ? segments : std::max<int64_t>(1, std::min<int64_t>(auto_runs, nb / 1024));
   want = std::min<int64_t>(std::min<int64_t>(want, kHostMaxSegments), nb);
   int64_t bps = ceil_div(nb, want);
   bps += bps & 1;  // whole pairs per run
