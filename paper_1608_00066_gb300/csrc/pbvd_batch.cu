@@ -80,10 +80,13 @@ cudaError_t batch_occupancy(int* blocks, int cta, size_t smem) {
 }
 
 // Batches of a single code: one persistent kernel with only that code's
-// path, so that it gets that path's register budget (eight 64-thread CTAs
-// per SM) instead of the largest of three.
-template <class C, int T, bool PUNCT>
-__global__ void __launch_bounds__(64, 8) pbvd_batch_single_kernel(const BatchArgs b, const int slot) {
+// path, so that it gets that path's register budget (MINB 64-thread CTAs
+// per SM) instead of the largest of three.  K=7 r1/2 runs at two threads
+// per pair with six CTAs per SM (168 registers): a batch of 10,000 frames
+// then fits in about one wave (66 against 62 Gb/s at four threads per pair
+// and eight CTAs, measured).
+template <class C, int T, bool PUNCT, int MINB>
+__global__ void __launch_bounds__(64, MINB) pbvd_batch_single_kernel(const BatchArgs b, const int slot) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int s_tile;
   for (;;) {
@@ -97,9 +100,9 @@ __global__ void __launch_bounds__(64, 8) pbvd_batch_single_kernel(const BatchArg
   }
 }
 
-#define PBVD_SINGLE0 K7, 4, false
-#define PBVD_SINGLE1 K7, 4, true
-#define PBVD_SINGLE2 K9, 8, false
+#define PBVD_SINGLE0 K7, 2, false, 6
+#define PBVD_SINGLE1 K7, 4, true, 8
+#define PBVD_SINGLE2 K9, 8, false, 8
 
 cudaError_t launch_single(const BatchArgs& a, int slot, int grid, int cta, size_t smem, cudaStream_t s) {
   if (slot == 0)
@@ -130,7 +133,7 @@ cudaError_t single_occupancy(int slot, int* blocks, int cta, size_t smem) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pbvd_batch_single_kernel<PBVD_SINGLE2>, cta, smem);
 }
 
-template <class C, int T, bool P>
+template <class C, int T, bool P, int MINB>
 void fill_single(BatchKernelEntry& e, int s) {
   e.single_T[s] = T;
   e.single_words_per_stage[s] = record_words_per_stage<C, T>();
