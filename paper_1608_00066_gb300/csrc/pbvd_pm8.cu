@@ -31,8 +31,10 @@
 // takes an unreachable predecessor, and the traceback (from S_0, along
 // reachable states only) reads none of the decisions of unreachable states.
 //
-// Layout: thread = quad of four consecutive blocks 4q .. 4q+3, block l in byte
-// l of every register; the quad runs in lock step over I = min(D + 2L, n)
+// Layout: a quad of four consecutive blocks 4q .. 4q+3, block l in byte l of
+// every register, is decoded by one thread (pm8_decode_kernel) or by two
+// that split its states (pm8_decode2_kernel, 64-state codes); the quad runs
+// in lock step over I = min(D + 2L, n)
 // stages, each block over its own [f0, f1] from stage index 0, padded with
 // neutral values (a = Q: every codeword the same metric) after its end.  A
 // gather kernel first writes the biased values of the four blocks of every
@@ -43,8 +45,8 @@
 // returns to the start after v stages, so the compiler keeps every metric in
 // place).  Survivor records: per stage and quad N/8 words, word w bit 8l + k =
 // 1 iff state 8w + k of block l kept its upper predecessor S_{2j}.  The
-// traceback walks the four chains together over records staged in a
-// per-thread shared-memory ring (cp.async), one thread per quad.
+// traceback walks the chains (four per thread, or two per lane of a pair)
+// over records staged in a per-thread shared-memory ring (cp.async).
 #include <cstdint>
 #include <cuda_runtime.h>
 
