@@ -380,6 +380,15 @@ PBVD_API int pbvd_stream_close(pbvd_stream *s, void *stream);
  * far have completed on their CUDA stream. */
 PBVD_API int64_t pbvd_stream_released(const pbvd_stream *s);
 
+/* Inspection of a stream's carried state (for tests and tools): copies the
+ * N = 2^{K-1} path metrics the stream holds after its last decoded stage to
+ * h_metrics (state order, host memory) and the number of stages decoded so
+ * far (whole periods; a partial period waits in the carry buffer) to
+ * *stages.  The metrics are renormalised 16-bit values: they equal Eq. (1)'s
+ * exact metrics of those stages up to one common offset.  Waits for the work
+ * queued on `stream` before the copy. */
+PBVD_API int pbvd_stream_metrics(const pbvd_stream *s, int64_t *stages, int32_t *h_metrics, void *stream);
+
 /* Frees the stream's device state (synchronises the device first). */
 PBVD_API void pbvd_stream_destroy(pbvd_stream *s);
 

@@ -1454,6 +1454,18 @@ void pbvd_stream_destroy(pbvd_stream* s) {
 
 int64_t pbvd_stream_released(const pbvd_stream* s) { return s ? s->released : -1; }
 
+int pbvd_stream_metrics(const pbvd_stream* s, int64_t* stages, int32_t* h_metrics, void* stream) {
+  if (!s || !stages || !h_metrics) return PBVD_EINVAL;
+  const int N = s->ctx->N;
+  std::vector<uint32_t> w((size_t)N);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PBVD_CUDA(cudaMemcpyAsync(w.data(), s->d_pm, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, st));
+  PBVD_CUDA(cudaStreamSynchronize(st));
+  for (int u = 0; u < N; ++u) h_metrics[u] = (int32_t)(w[u] & 0xFFFFu);  // lane A, natural state order
+  *stages = s->t;
+  return PBVD_OK;
+}
+
 int pbvd_stream_push_many(pbvd_stream* const* ss, const int8_t* const* d_llr, const size_t* n_stages,
                           size_t count, int close, void* stream) {
   if (!ss || count == 0) return PBVD_EINVAL;

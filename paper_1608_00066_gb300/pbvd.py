@@ -37,7 +37,7 @@ EXPORTS = (
     "pbvd_stream_open", "pbvd_stream_push", "pbvd_stream_push_many", "pbvd_stream_close",
     "pbvd_stream_released", "pbvd_stream_destroy", "pbvd_batch_update", "pbvd_decode_host",
     "pbvd_decode_packed", "pbvd_decode_host_packed", "pbvd_set_mode", "pbvd_get_mode",
-    "pbvd_decode_two_kernel", "pbvd_decode_packed_pm8", "pbvd_measure_int_rate",
+    "pbvd_decode_two_kernel", "pbvd_decode_packed_pm8", "pbvd_measure_int_rate", "pbvd_stream_metrics",
 )
 
 PBVD_MODE_ARGMIN = 1
@@ -143,6 +143,8 @@ def load(path: Optional[str] = None):
         lib.pbvd_stream_close.restype = I
         lib.pbvd_stream_released.argtypes = [V]
         lib.pbvd_stream_released.restype = ctypes.c_int64
+        lib.pbvd_stream_metrics.argtypes = [V, ctypes.POINTER(ctypes.c_int64), V, V]
+        lib.pbvd_stream_metrics.restype = I
         lib.pbvd_stream_destroy.argtypes = [V]
         lib.pbvd_stream_destroy.restype = None
         _lib = lib
@@ -358,6 +360,16 @@ def pbvd_stream_released(s: int) -> int:
     return int(load().pbvd_stream_released(s))
 
 
+def pbvd_stream_metrics(s: int, n_states: int, stream: int = 0):
+    """(stages decoded, int32 array of the carried path metrics in state
+    order) of a stream; waits for the work queued on `stream`."""
+    import numpy as np
+    out = np.zeros(n_states, dtype=np.int32)
+    t = ctypes.c_int64()
+    _check(load().pbvd_stream_metrics(s, ctypes.byref(t), out.ctypes.data, stream or None), "pbvd_stream_metrics")
+    return int(t.value), out
+
+
 def pbvd_stream_destroy(s: int) -> None:
     load().pbvd_stream_destroy(s)
 
@@ -516,6 +528,12 @@ class Stream:
         import torch
         s = stream if stream is not None else torch.cuda.current_stream(self.out.device)
         pbvd_stream_close(self.handle, s.cuda_stream)
+
+    def metrics(self, stream=None):
+        """(stages decoded, carried path metrics in state order)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.out.device)
+        return pbvd_stream_metrics(self.handle, 1 << (self.decoder.K - 1), s.cuda_stream)
 
     def destroy(self):
         if self.handle:

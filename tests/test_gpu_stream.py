@@ -210,3 +210,38 @@ def test_stream_errors():
     del ctypes
     for d in (dec, dp, d3):
         d.close()
+
+
+@pytest.mark.parametrize("name", STREAM_CODES)
+def test_carried_metrics_equal_oracle_up_to_a_shift(name):
+    """The stream's 16-bit renormalised path metrics after every push equal
+    the oracle's exact int64 metrics of Eq. (1) after the same stage (known
+    start S_0, full-frame form) up to one common offset per stage, over
+    pushes of uneven sizes, noisy and noiseless stretches and the first
+    stages where only part of the states are reachable."""
+    spec = synth.CODES[name]
+    rng = np.random.default_rng(31 + spec.K)
+    n = 20000
+    f = synth.make_frame(spec, n - spec.v, 1.0, seed=spec.K)
+    llr = np.asarray(f.llr, np.int8).reshape(n, spec.R).copy()
+    llr[8000:9000] = rng.integers(-127, 128, size=(1000, spec.R), dtype=np.int16).astype(np.int8)
+    _, _, _, pm_trace = oracle.viterbi_full(spec.K, spec.gens, llr, want_trace=True)
+    dec = pbvd.Decoder(spec.K, spec.gens, None, 512, 42)
+    st = pbvd.Stream(dec, n, 4096)
+    d = torch.from_numpy(llr.reshape(-1)).cuda()
+    t, checked = 0, 0
+    for c in [1, 2, 3, 5, 7, 64, 1000, 4096, 300, 4096, 4096, 4096, 2000]:
+        c = min(c, n - t)
+        if c == 0:
+            break
+        st.push(d[t * spec.R:(t + c) * spec.R], c)
+        t += c
+        done, pm = st.metrics()
+        if done == 0:
+            continue
+        want = pm_trace[done - 1]
+        assert np.array_equal(pm.astype(np.int64) - pm[0], want - want[0]), (name, done)
+        checked += 1
+    assert checked >= 8
+    st.destroy()
+    dec.close()
