@@ -881,28 +881,43 @@ __device__ __forceinline__ void tb_walk4(const KArgs& a, int64_t gslot, const ui
   // block k holds records atop - k P - u, u = 0..P-1, at phases P-1-u
   const int atop = hs + (P - 1 - (L + hs) % P);
   const int nblk = (atop - lo) / P + 1;
+  // Global mode: the next block to request starts at record jq, whose word
+  // offset in the workspace is offq; consecutive records of a slot lie
+  // 'stride' words apart, so the offsets are kept running (no per-record
+  // multiply) and so are the ring positions of the next request (iq) and of
+  // the next block walked (ic).
   const int64_t stride = a.surv_pairs * (int64_t)a.surv_rs;
-  int issued = 0;
+  int64_t offq = ((int64_t)atop * a.surv_pairs + gslot) * a.surv_rs;
+  int jq = atop;
+  int iq = 0, ic = 0;
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
   auto issue = [&]() {
     if constexpr (!SMEM) {
-      if (issued < nblk) {
-        uint32_t* dst0 = ring + (issued % NBUF) * (P * 4);
-        const int j0 = atop - issued * P;
+      if (jq >= lo) {
+        const unsigned d0 = ring_s + (unsigned)iq * (P * 16);
+        const uint32_t* src = a.surv + offq;
+        if (jq <= hs && jq - (P - 1) >= lo) {
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-          const int j = j0 - u;
-          if (j >= lo && j <= hs) {
-            const unsigned d = (unsigned)__cvta_generic_to_shared(dst0 + u * 4);
-            const uint32_t* src = a.surv + ((int64_t)j * a.surv_pairs + gslot) * a.surv_rs;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+          for (int u = 0; u < P; ++u) {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16 * u), "l"(src));
+            src -= stride;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < P; ++u) {
+            const int j = jq - u;
+            if (j >= lo && j <= hs)
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16 * u), "l"(src));
+            src -= stride;
           }
         }
       }
-      ++issued;
+      offq -= P * stride;
+      jq -= P;
+      iq = (iq + 1 == NBUF) ? 0 : iq + 1;
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
   };
-  (void)stride;
 #pragma unroll
   for (int q = 0; q < NBUF - 1; ++q) issue();
   for (int k = 0; k < nblk; ++k) {
@@ -915,7 +930,8 @@ __device__ __forceinline__ void tb_walk4(const KArgs& a, int64_t gslot, const ui
     } else {
       issue();
       asm volatile("cp.async.wait_group %0;" ::"n"(NBUF - 1) : "memory");
-      blk = ring + (k % NBUF) * (P * 4);
+      blk = ring + ic * (P * 4);
+      ic = (ic + 1 == NBUF) ? 0 : ic + 1;
       bstep = 4;
     }
     const int jb = max(lo, j0 - P + 1);
@@ -923,8 +939,11 @@ __device__ __forceinline__ void tb_walk4(const KArgs& a, int64_t gslot, const ui
     uint4 rec[P];
 #pragma unroll
     for (int u = 0; u < P; ++u) {
+      // a ring slot always lies inside the lane's ring (records outside
+      // [lo, hs] are loaded but never walked); the shared-memory survivor
+      // region is read only inside the group's records
       const int j = j0 - u;
-      if (j >= lo && j <= hs) rec[u] = *reinterpret_cast<const uint4*>(blk + u * bstep);
+      if (!SMEM || full || (j >= lo && j <= hs)) rec[u] = *reinterpret_cast<const uint4*>(blk + u * bstep);
     }
     auto step = [&](auto phc, int u, bool guarded) {
       constexpr int PH = decltype(phc)::value;
