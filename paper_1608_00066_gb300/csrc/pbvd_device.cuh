@@ -169,7 +169,7 @@ __host__ __device__ constexpr int tb_nbuf() {
 // traceback: every lane walks both PBs of its pair (two chains) over 1/T of
 // the records, rather than half the lanes per PB
 template <class C, int T>
-__host__ __device__ constexpr bool tb_both_pbs() { return T >= 4; }
+__host__ __device__ constexpr bool tb_both_pbs() { return T >= 2; }
 template <class C, int T>
 __host__ __device__ constexpr int scratch_words_per_group() {
   using S = Shape<C, T>;
@@ -843,13 +843,16 @@ __device__ __forceinline__ uint32_t conv4(uint32_t psi) {
 }
 
 // One traceback step at a record of compile-time phase PH: appends the
-// decoded bit (bit PH of psi) to acc and moves psi to the predecessor (bit
-// PH replaced by the survivor's branch, then the period rotation at PH = 0).
-template <class C, int T, int PH>
+// decoded bit (bit PH of psi) to acc (ACC) and moves psi to the predecessor
+// (bit PH replaced by the survivor's branch, then the period rotation at
+// PH = 0).  Over a whole period (phases P-1 .. 0) step PH reads bit PH
+// before any step changes it, so the period's P decoded bits are the low P
+// bits of psi on entry; the unguarded walk appends them once per period.
+template <class C, int T, int PH, bool ACC = true>
 __device__ __forceinline__ void tb_step_ph(uint32_t& psi, uint32_t& acc, uint64_t G) {
   constexpr int P = Shape<C, T>::P;
   const uint32_t upper = (uint32_t)(G >> conv4<PH>(psi)) & 1u;
-  acc = (acc << 1) | ((psi >> PH) & 1u);
+  if constexpr (ACC) acc = (acc << 1) | ((psi >> PH) & 1u);
   uint32_t np = (psi & ~(1u << PH)) | ((upper ^ 1u) << PH);
   if constexpr (PH == 0) np = rotl_v<C::v>(np, P % C::v);
   psi = np;
@@ -945,18 +948,23 @@ __device__ __forceinline__ void tb_walk4(const KArgs& a, int64_t gslot, const ui
       const int j = j0 - u;
       if (!SMEM || full || (j >= lo && j <= hs)) rec[u] = *reinterpret_cast<const uint4*>(blk + u * bstep);
     }
-    auto step = [&](auto phc, int u, bool guarded) {
+    auto step = [&](auto phc, int u, auto guarded) {
       constexpr int PH = decltype(phc)::value;
+      constexpr bool G = decltype(guarded)::value != 0;
       const int j = j0 - u;
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
-        if (!guarded || (j >= lo && j <= hs && j <= jend[c])) {
-          if (guarded && j == g_at) g[c] = (int)ps[c];
-          tb_step_ph<C, T, PH>(ps[c], acc[c], gather4<PH>(rec[u], x[c]));
+        if (!G || (j >= lo && j <= hs && j <= jend[c])) {
+          if (G && j == g_at) g[c] = (int)ps[c];
+          tb_step_ph<C, T, PH, G>(ps[c], acc[c], gather4<PH>(rec[u], x[c]));
         }
       }
     };
-    auto run_block = [&](bool guarded) {
+    auto run_block = [&](auto guarded) {
+      if constexpr (decltype(guarded)::value == 0) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) acc[c] = (acc[c] << P) | (ps[c] & ((1u << P) - 1u));
+      }
       if constexpr (P > 5) step(IntC<(P > 5 ? P - 6 : 0) + 5>{}, P - 6, guarded);
       if constexpr (P > 4) step(IntC<4>{}, P - 5, guarded);
       step(IntC<3>{}, P - 4, guarded);
@@ -964,7 +972,7 @@ __device__ __forceinline__ void tb_walk4(const KArgs& a, int64_t gslot, const ui
       step(IntC<1>{}, P - 2, guarded);
       step(IntC<0>{}, P - 1, guarded);
     };
-    if (full) run_block(false); else run_block(true);
+    if (full) run_block(IntC<0>{}); else run_block(IntC<1>{});
     // the byte whose lowest record (a multiple of 8) lies in this block
     const int m8 = (j0 >> 3) << 3;
     if (m8 >= jb && m8 <= hs) {
