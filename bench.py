@@ -387,10 +387,14 @@ def run_ours(args, rank: int, world: int):
     # flight (two contexts on two CUDA streams, alternating), so that one
     # call's copies overlap the other's decoding; every step still copies its
     # own soft values in and its bits out
+    # the second context mirrors the first: the same explicit configuration
+    # (--tune, --autotune), else the library's automatic one, which for host
+    # calls is the pipelined form (a configuration fixed to pbvd_decode's
+    # would mix two kernel shapes on the SMs)
     dec_b = pbvd.Decoder(spec.K, spec.gens, None, D_BLOCK, L_OVERLAP)
     if args.tune:
         dec_b.set_config(**json.loads(args.tune))
-    else:
+    elif args.autotune:
         dec_b.set_config(**cfg)
     stream_b = torch.cuda.Stream()
     h_llr_b = torch.from_numpy(frame.llr.copy()).pin_memory()

@@ -195,9 +195,21 @@ struct Plan {
   size_t surv_bytes;     // global-mode survivor bytes
 };
 
-int states_max_per_thread() { return 64; }
+// At most 64 states per thread for codes of up to 64 states, 32 above (the
+// 256-state code at four threads per pair, 64 states each, decodes the
+// 2^24-bit stream 16% slower than at eight).
+int states_max_per_thread(int N) { return N > 64 ? 32 : 64; }
 
-int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p) {
+// Automatic kernel configuration.  The throughput form (pbvd_decode) takes
+// the fewest threads per pair that still give about 1.5 warps per scheduler:
+// fewer threads per pair execute fewer instructions per butterfly (branch
+// metrics, transposes, traceback shared by more states), and 1.5 warps
+// hide enough latency (K=7 2^24-bit stream at D = 512: two threads per pair
+// in 32-thread CTAs 0.2235 ms, four in 64-thread CTAs 0.2309 ms).  The
+// pipelined form (pbvd_decode_host, whose runs each end a pair's dependency
+// chain after their copy) aims at about 2 warps per scheduler, which gives
+// shorter chains (the same stream from host memory: 46.6 against 42.1 Gb/s).
+int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p, bool pipelined = false) {
   Registry& reg = registry();
   const bool var = c->mode != 0;
   p->n_blocks = ceil_div((int64_t)n_stages, c->D);
@@ -205,8 +217,9 @@ int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p) {
   int T = c->cfg.threads_per_pair;
   if (T <= 0) {
     int tmin = 1;
-    while (c->N / tmin > states_max_per_thread()) tmin *= 2;
-    const int64_t target = (int64_t)c->sm_count * 4 * 2 * 32;  // ~2 warps per scheduler
+    while (c->N / tmin > states_max_per_thread(c->N)) tmin *= 2;
+    // threads for ~1.5 (throughput) or ~2 (pipelined) warps per scheduler
+    const int64_t target = (int64_t)c->sm_count * 4 * 32 * (pipelined ? 4 : 3) / 2;
     int64_t want = ceil_div(target, std::max<int64_t>(p->n_pairs, 1));
     T = 1;
     while (T < want && T < 32) T *= 2;
@@ -230,7 +243,9 @@ int plan_decode(const pbvd_ctx* c, size_t n_stages, Plan* p) {
   }
   p->smem_surv = smem;
   int cta = c->cfg.cta_threads;
-  if (cta <= 0) cta = smem ? T : std::max(T, 64);
+  // one-warp CTAs at one or two threads per pair (a warp already holds 16
+  // or 32 pairs; measured faster than two-warp CTAs there), else 64 threads
+  if (cta <= 0) cta = smem ? T : ((!pipelined && T <= 2) ? 32 : std::max(T, 64));
   if (cta % T != 0 || cta > 256 || cta < T) return PBVD_EINVAL;
   p->cta = cta;
   p->groups = cta / T;
@@ -818,11 +833,15 @@ int pbvd_get_config(const pbvd_ctx* c, size_t n_stages, pbvd_config* cfg) {
   return PBVD_OK;
 }
 
-int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_out, void* stream) {
+// The decode of pbvd_decode; 'pipelined' selects the automatic configuration
+// of host calls (direct access: the kernel's reads of host memory need many
+// warps in flight).
+static int decode_device(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_out, void* stream,
+                         bool pipelined) {
   if (!c || !d_llr || !d_out || n_stages == 0) return PBVD_EINVAL;
   if (n_stages > ((size_t)1 << 40)) return PBVD_EINVAL;
   Plan p;
-  int rc = plan_decode(c, n_stages, &p);
+  int rc = plan_decode(c, n_stages, &p, pipelined);
   if (rc != PBVD_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int8_t* src = d_llr;
@@ -874,6 +893,10 @@ int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_ou
   if (grid > 0x7fffffff) return PBVD_EINVAL;
   const KernelEntry& e = registry().entries[p.entry];
   return entry_launch(e, p.smem_surv, a, (int)grid, p.cta, p.smem_bytes, st);
+}
+
+int pbvd_decode(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_out, void* stream) {
+  return decode_device(c, d_llr, n_stages, d_out, stream, false);
 }
 
 int pbvd_decode_two_kernel(pbvd_ctx* c, const int8_t* d_llr, size_t n_stages, uint8_t* d_out, void* stream) {
@@ -941,14 +964,14 @@ int decode_host_impl(pbvd_ctx* c, const void* h_in, int q, size_t n_stages, uint
     const int8_t* d_in = static_cast<const int8_t*>(mapped_host(h_llr));
     uint8_t* d_o = static_cast<uint8_t*>(mapped_host(h_out));
     if (!d_in || !d_o) return PBVD_EINVAL;
-    return pbvd_decode(c, d_in, n_stages, d_o, stream);
+    return decode_device(c, d_in, n_stages, d_o, stream, true);
   }
   // the kernel configuration pbvd_decode would use, survivors in global
   // memory (one workspace slice per compute lane)
   pbvd_ctx cc = *c;
   cc.cfg.survivors_in_smem = 0;
   Plan p;
-  int rc = plan_decode(&cc, n_stages, &p);
+  int rc = plan_decode(&cc, n_stages, &p, true);
   if (rc != PBVD_OK) return rc;
   const int64_t nb = p.n_blocks;
   // runs of whole pairs of blocks; automatic: up to 6 runs (fewer for packed
