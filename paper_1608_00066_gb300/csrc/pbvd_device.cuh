@@ -166,10 +166,6 @@ template <class C, int T>
 __host__ __device__ constexpr int tb_nbuf() {
   return tb_period_walk<C, T>() ? 1 + (24 + Shape<C, T>::P - 1) / Shape<C, T>::P : (T <= 2 ? 4 : 3);
 }
-// traceback: every lane walks both PBs of its pair (two chains) over 1/T of
-// the records, rather than half the lanes per PB
-template <class C, int T>
-__host__ __device__ constexpr bool tb_both_pbs() { return T >= 2; }
 template <class C, int T>
 __host__ __device__ constexpr int scratch_words_per_group() {
   using S = Shape<C, T>;
@@ -614,12 +610,12 @@ __device__ __forceinline__ void forward_period(uint32_t (&pm)[Shape<C, T>::M], c
 
 // ------------------------------------------------------------- traceback --
 
-// Traceback shape.  T == 1: the lane walks both PBs of its pair (two chains,
-// same records).  T >= 2: every lane walks one segment of one PB; a PB is
-// split into SPB segments of whole bytes, each non-top segment starting
-// LAMBDA records above its range from S_0 (a guess), then checked against
-// the exact exit state of the segment above and re-walked if it differs, so
-// the result is exact for any LAMBDA.
+// Traceback shape.  Every lane walks both PBs of its pair (two chains over
+// the same records).  T == 1: all records, from S_0.  T >= 2: the records
+// are split into T segments of whole bytes, lane tau walking segment tau;
+// each non-top segment starts LAMBDA records above its range from S_0 (a
+// guess), then is checked against the exact exit state of the segment above
+// and re-walked if it differs, so the result is exact for any LAMBDA.
 template <class C, int T>
 struct TbShape {
   static constexpr int RW = Shape<C, T>::RW;             // words per record
@@ -766,10 +762,12 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
   const int nchunk = (hs - lo) / KR + 1;
   const int64_t stride = a.surv_pairs * (int64_t)a.surv_rs;
   const uint32_t* src_next = global_record<C, T>(a, gslot, hs);
-  int issued = 0;
+  // ring positions of the next request (iq) and of the next chunk walked
+  // (ic), kept running
+  int issued = 0, iq = 0, ic = 0;
   auto issue = [&]() {
     if (issued < nchunk) {
-      uint32_t* dst0 = ring + (issued % NBUF) * (KR * RW);
+      uint32_t* dst0 = ring + iq * (KR * RW);
       const int jtop = hs - issued * KR;
 #pragma unroll
       for (int q = 0; q < KR; ++q) {
@@ -789,6 +787,7 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
       }
     }
     ++issued;
+    iq = (iq + 1 == NBUF) ? 0 : iq + 1;
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
 #pragma unroll
@@ -798,7 +797,8 @@ __device__ __forceinline__ void tb_walk(const KArgs& a, int64_t gslot, const uin
     asm volatile("cp.async.wait_group %0;" ::"n"(NBUF - 1) : "memory");
     const int jtop = hs - ch * KR;
     const int jbot = max(lo, jtop - KR + 1);
-    const uint32_t* buf = ring + (ch % NBUF) * (KR * RW);
+    const uint32_t* buf = ring + ic * (KR * RW);
+    ic = (ic + 1 == NBUF) ? 0 : ic + 1;
     if constexpr (RW == 4) {
       visit4(jtop, jbot, buf, RW);
     } else {
@@ -1028,18 +1028,14 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     int psi[2] = {start[0], start[1]}, g[2];
     tb_walk_any<C, T, SMEM, 2>(a, gslot, svs, ring, L, max(jA, jB), 0, emit_top, jend, x, nout, dst, -1, psi, g);
   } else {
-    // Segments: lane tau walks segment s of the records of one or both PBs.
-    // With BOTH, every lane walks both PBs of the pair (two chains over the
-    // same records, two independent dependency chains per lane) over T
-    // segments; otherwise lanes [0, T/2) walk PB A and [T/2, T) PB B, one
-    // chain each (all lanes walk A when there is no B).
-    constexpr bool BOTH = tb_both_pbs<C, T>();
+    // Segments: lane tau walks segment tau of the records of both PBs of
+    // the pair (two chains over the same records: two independent dependency
+    // chains per lane, one record stream; measured faster than half the
+    // lanes per PB at two and four threads per pair).
     const int jA = gA.iend - L, jB = hasB ? gB.iend - L : -1;
-    const int SPB = BOTH ? T : (hasB ? T / 2 : T);
-    const int xb = (!BOTH && hasB && tau >= SPB) ? 1 : 0;
-    const int s = tau - xb * SPB;
-    const int jtop = BOTH ? max(jA, jB) : (xb ? jB : jA);
-    const int seg = (((jtop + 1 + SPB - 1) / SPB) + 7) & ~7;
+    const int s = tau;
+    const int jtop = max(jA, jB);
+    const int seg = (((jtop + 1 + T - 1) / T) + 7) & ~7;
     const int lo = s * seg;
     const int hi = min(jtop, lo + seg - 1);
     const int stop = jtop / seg;    // top non-empty segment
@@ -1049,25 +1045,12 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     // begin with a guess (the same state), checked below
     int psi[2] = {start[0], start[1]}, g[2] = {0, 0};
     if (active) {
-      if constexpr (BOTH) {
-        const int emit_top[2] = {min(hi, gA.nout - 1), min(hi, gB.nout - 1)};
-        const int je[2] = {jA, jB};
-        const int x[2] = {0, 1};
-        const int nout[2] = {gA.nout, gB.nout};
-        uint8_t* const dst[2] = {gA.dst, gB.dst};
-        tb_walk_any<C, T, SMEM, 2>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
-      } else {
-        const PbRun& g0 = xb ? gB : gA;
-        const int emit_top[1] = {min(hi, g0.nout - 1)};
-        const int je[1] = {jtop};
-        const int x[1] = {xb};
-        const int nout[1] = {g0.nout};
-        uint8_t* const dst[1] = {g0.dst};
-        int p1[1] = {xb ? start[1] : start[0]}, g1[1] = {0};
-        tb_walk_any<C, T, SMEM, 1>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, p1, g1);
-        psi[0] = p1[0];
-        g[0] = g1[0];
-      }
+      const int emit_top[2] = {min(hi, gA.nout - 1), min(hi, gB.nout - 1)};
+      const int je[2] = {jA, jB};
+      const int x[2] = {0, 1};
+      const int nout[2] = {gA.nout, gB.nout};
+      uint8_t* const dst[2] = {gA.dst, gB.dst};
+      tb_walk_any<C, T, SMEM, 2>(a, gslot, svs, ring, L, hs, lo, emit_top, je, x, nout, dst, hi, psi, g);
     }
     // One parallel round first: every guessed segment whose entry state
     // differs from the exit state of the first walk of the segment above is
@@ -1078,13 +1061,12 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     for (int pb = 0; pb < (PAR ? (hasB ? 2 : 1) : 0); ++pb) {
       const PbRun& gp = pb ? gB : gA;
       const int jend_p = pb ? jB : jA;
-      const int seg_p = BOTH ? seg : (((jend_p + 1 + SPB - 1) / SPB) + 7) & ~7;
+      const int seg_p = seg;
       const int top = jend_p / seg_p;
-      const int base = BOTH ? 0 : pb * SPB;
-      const int c = BOTH ? pb : 0;
-      const int q = tau - base;
+      const int c = pb;  // chain of this PB in every lane
+      const int q = tau;
       const int above = __shfl_sync(gmask, c ? psi[1] : psi[0], (tau + 1) & (T - 1), T);
-      const bool redo = (BOTH || xb == pb) && q < top && above != (c ? g[1] : g[0]);
+      const bool redo = q < top && above != (c ? g[1] : g[0]);
       if (redo) {
         const int lo_q = q * seg_p, hi_q = min(jend_p, lo_q + seg_p - 1);
         int p2[1] = {above}, g2[1];
@@ -1104,10 +1086,10 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     for (int pb = 0; pb < (hasB ? 2 : 1); ++pb) {
       const PbRun& gp = pb ? gB : gA;
       const int jend_p = pb ? jB : jA;
-      const int seg_p = BOTH ? seg : (((jend_p + 1 + SPB - 1) / SPB) + 7) & ~7;
+      const int seg_p = seg;
       const int top = jend_p / seg_p;
-      const int base = BOTH ? 0 : pb * SPB;   // lane of segment 0
-      const int c = BOTH ? pb : 0;            // chain of this PB in its lanes
+      const int base = 0;  // lane of segment 0
+      const int c = pb;    // chain of this PB in every lane
       int exact = __shfl_sync(gmask, c ? psi[1] : psi[0], base + top, T);
       for (int q = top - 1; q >= 0; --q) {
         const int gq = __shfl_sync(gmask, c ? g[1] : g[0], base + q, T);
