@@ -288,7 +288,14 @@ PBVD_API void pbvd_batch_destroy(pbvd_batch *batch);
  *                     N/T states per thread); 0 = automatic
  *   cta_threads       threads per CTA (multiple of 32, <= 256); 0 = automatic
  *   survivors_in_smem 1: survivor bits in shared memory, 0: in the device
- *                     workspace, -1 = automatic */
+ *                     workspace, -1 = automatic
+ * Automatic: pbvd_decode (and the calls built on it) takes the fewest
+ * threads per pair that give about 1.5 warps per SM scheduler, with at most
+ * 64 states per thread (32 for codes of more than 64 states), in one-warp
+ * CTAs when T <= 2 and 64-thread CTAs otherwise; pbvd_decode_host (its copy
+ * pipeline and its direct access) aims at about 2 warps per scheduler in
+ * CTAs of at least 64 threads, which shortens each run's dependency chain;
+ * survivors go to shared memory when there are no more pairs than SMs. */
 typedef struct pbvd_config {
     int threads_per_pair;
     int cta_threads;
@@ -299,7 +306,8 @@ typedef struct pbvd_config {
  * PBVD_EUNSUPPORTED if the code has no kernel for that T. */
 PBVD_API int pbvd_set_config(pbvd_ctx *ctx, const pbvd_config *cfg);
 
-/* Reads back the configuration pbvd_decode would use for n_stages. */
+/* Reads back the configuration pbvd_decode would use for n_stages (with an
+ * automatic configuration, pbvd_decode_host may use more threads per pair). */
 PBVD_API int pbvd_get_config(const pbvd_ctx *ctx, size_t n_stages, pbvd_config *cfg);
 
 /* Autotuner (not in the paper): decodes the caller's data with every built
