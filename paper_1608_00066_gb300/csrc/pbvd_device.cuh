@@ -1055,28 +1055,37 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     // One parallel round first: every guessed segment whose entry state
     // differs from the exit state of the first walk of the segment above is
     // walked again from that state, all such segments at once in their own
-    // lanes.  The exit of a segment above is exact unless that segment was
-    // itself walked again and ended elsewhere, which the top-down check below
-    // finds (and walks again, one segment after another) as before.
-    for (int pb = 0; pb < (PAR ? (hasB ? 2 : 1) : 0); ++pb) {
-      const PbRun& gp = pb ? gB : gA;
-      const int jend_p = pb ? jB : jA;
-      const int seg_p = seg;
-      const int top = jend_p / seg_p;
-      const int c = pb;  // chain of this PB in every lane
-      const int q = tau;
-      const int above = __shfl_sync(gmask, c ? psi[1] : psi[0], (tau + 1) & (T - 1), T);
-      const bool redo = q < top && above != (c ? g[1] : g[0]);
-      if (redo) {
-        const int lo_q = q * seg_p, hi_q = min(jend_p, lo_q + seg_p - 1);
-        int p2[1] = {above}, g2[1];
-        const int emit_top[1] = {min(hi_q, gp.nout - 1)};
-        const int je[1] = {jend_p};
-        const int x[1] = {pb};
-        const int nout[1] = {gp.nout};
-        uint8_t* const dst[1] = {gp.dst};
-        tb_walk_any<C, T, SMEM, 1>(a, gslot, svs, ring, L, hi_q, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
-        if (c) { psi[1] = p2[0]; g[1] = above; } else { psi[0] = p2[0]; g[0] = above; }
+    // lanes, and both PBs of a lane in one two-chain walk over their common
+    // records (a chain that needs no second walk writes nothing).  The exit
+    // of a segment above is exact unless that segment was itself walked
+    // again and ended elsewhere, which the top-down check below finds (and
+    // walks again, one segment after another) as before.
+    if constexpr (PAR) {
+      const int topA = jA / seg, topB = hasB ? jB / seg : -1;
+      const int src = (tau + 1) & (T - 1);
+      const int aboveA = __shfl_sync(gmask, psi[0], src, T);
+      const int aboveB = __shfl_sync(gmask, psi[1], src, T);
+      const bool redoA = tau < topA && aboveA != g[0];
+      const bool redoB = hasB && tau < topB && aboveB != g[1];
+      if (redoA || redoB) {
+        const int lo_q = tau * seg;
+        const int hiA = min(jA, lo_q + seg - 1), hiB = min(jB, lo_q + seg - 1);
+        int p2[2] = {aboveA, aboveB}, g2[2];
+        const int emit_top[2] = {redoA ? min(hiA, gA.nout - 1) : -1, redoB ? min(hiB, gB.nout - 1) : -1};
+        const int je[2] = {jA, jB};
+        const int x[2] = {0, 1};
+        const int nout[2] = {gA.nout, gB.nout};
+        uint8_t* const dst[2] = {gA.dst, gB.dst};
+        const int hs2 = max(redoA ? hiA : -1, redoB ? hiB : -1);
+        tb_walk_any<C, T, SMEM, 2>(a, gslot, svs, ring, L, hs2, lo_q, emit_top, je, x, nout, dst, -1, p2, g2);
+        if (redoA) {
+          psi[0] = p2[0];
+          g[0] = aboveA;
+        }
+        if (redoB) {
+          psi[1] = p2[1];
+          g[1] = aboveB;
+        }
       }
     }
     // top-down check of the guessed segments of each PB: segment q is exact

@@ -50,3 +50,37 @@ def test_batch_geometry_tuner_choice_matches_oracle():
         D, L = choice[f.spec.name]
         want = oracle.viterbi_block(f.spec.K, f.spec.gens, mother_llr(f.spec, f.llr, f.n_stages), D, L)
         assert np.array_equal(np.unpackbits(o.cpu().numpy(), bitorder="little")[:f.n_stages], want)
+
+
+def _auto_threads(N, pairs, sms):
+    """The documented automatic rule of a device decode: the fewest threads
+    per pair (a power of two) that give about 1.5 warps per SM scheduler,
+    with at most 64 states per thread (32 above 64 states)."""
+    tmin = 1
+    while N // tmin > (32 if N > 64 else 64):
+        tmin *= 2
+    want = -(-(sms * 4 * 32 * 3 // 2) // pairs)
+    T = 1
+    while T < want and T < 32:
+        T *= 2
+    return min(max(T, tmin), 32, N // 2)
+
+
+@pytest.mark.parametrize("spec,D", [(synth.K7_R12, 512), (synth.K7_R12, 256), (synth.K9_R13, 1024)])
+def test_automatic_configuration_follows_the_documented_rule(spec, D):
+    """pbvd_get_config reports the rule the header documents: at the
+    2^24-bit stream's size two threads per pair in one-warp CTAs for the
+    64-state code at D = 512, one at D = 256, eight for the 256-state code;
+    shorter streams take more threads per pair."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    dec = pbvd.Decoder(spec.K, spec.gens, None, D, 42)
+    for n in (1 << 24, 1 << 22, 1 << 20):
+        pairs = -(-(-(-n // D)) // 2)
+        cfg = dec.get_config(n)
+        T = _auto_threads(1 << (spec.K - 1), pairs, sms)
+        if pairs <= sms:
+            continue  # few pairs: shared-memory survivors, CTA of one group
+        assert cfg["threads_per_pair"] == T, (n, cfg, T)
+        assert cfg["survivors_in_smem"] == 0
+        assert cfg["cta_threads"] == (32 if T <= 2 else max(T, 64)), (n, cfg)
+    dec.close()
