@@ -22,3 +22,26 @@ def test_reference_arm_json_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert "D=512" in line["config"]["workload"] and line["config"]["L"] == 42
+
+
+def test_roofline_bookkeeping():
+    """The DRAM traffic record is reported only for the kernel configuration
+    and device sources it was captured with, and the roofline arithmetic
+    matches the documented formulas."""
+    sys.path.insert(0, ROOT)
+    import bench
+    key, rec = next(iter(bench.PROFILED_TRAFFIC.items()))
+    if rec["sources"] == bench.kernel_sources_hash():
+        assert bench.profiled_traffic(key) == rec["bytes"]
+    assert bench.profiled_traffic((key[0] * 2, key[1], key[2])) is None
+    saved = rec["sources"]
+    try:
+        rec["sources"] = "0" * 16
+        assert bench.profiled_traffic(key) is None
+    finally:
+        rec["sources"] = saved
+    # 3N integer operations per state and stage, times the overlap (D + 2L) / D
+    assert abs(bench.algorithmic_ops_per_bit(64, 512, 42) - 223.5) < 1e-9
+    assert abs(bench.algorithmic_ops_per_bit(256, 1024, 64) - 864.0) < 1e-9
+    # 152 SMs x 4 schedulers x 32 lanes x 2 (16x2) x 2.07 GHz
+    assert abs(bench.peak_int16_ops(152, 2.07e9) - 80.54784e12) < 1e6
