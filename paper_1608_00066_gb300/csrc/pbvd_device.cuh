@@ -1035,10 +1035,21 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     const int jA = gA.iend - L, jB = hasB ? gB.iend - L : -1;
     const int s = tau;
     const int jtop = max(jA, jB);
-    const int seg = (((jtop + 1 + T - 1) / T) + 7) & ~7;
+    // Segment length (whole bytes): a lower segment is walked with LAMBDA
+    // records of warm-up above it and the top one exactly, so the lower
+    // segments take (J - LAMBDA) / T records each and the top one the rest,
+    // which evens out the lanes' walks (K=7, D = 512, L = 42: 304 and 306
+    // records at two threads per pair instead of 336 and 274).  Below
+    // 2 LAMBDA records the even split J / T is kept: at low Eb/N0 a walk
+    // from the exact state then often has not met the first walk's path by
+    // the end of so short a segment, and every such exit sends the segment
+    // below to a serial re-walk (eight threads per pair at 0 dB: 0.414
+    // against 0.393 ms).
+    const int seg_bal = (((jtop + 1 - TS::LAMBDA) / T) + 4) & ~7;
+    const int seg = seg_bal >= 2 * TS::LAMBDA ? seg_bal : (((jtop + 1 + T - 1) / T) + 7) & ~7;
+    const int stop = min(T - 1, jtop / seg);  // top non-empty segment
     const int lo = s * seg;
-    const int hi = min(jtop, lo + seg - 1);
-    const int stop = jtop / seg;    // top non-empty segment
+    const int hi = (s == stop) ? jtop : min(jtop, lo + seg - 1);
     const bool active = lo <= jtop;
     const int hs = (s == stop) ? jtop : min(jtop, hi + TS::LAMBDA);
     // a walk that begins at its PB's last record starts exactly; the others
@@ -1061,7 +1072,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
     // again and ended elsewhere, which the top-down check below finds (and
     // walks again, one segment after another) as before.
     if constexpr (PAR) {
-      const int topA = jA / seg, topB = hasB ? jB / seg : -1;
+      const int topA = min(T - 1, jA / seg), topB = hasB ? min(T - 1, jB / seg) : -1;
       const int src = (tau + 1) & (T - 1);
       const int aboveA = __shfl_sync(gmask, psi[0], src, T);
       const int aboveB = __shfl_sync(gmask, psi[1], src, T);
@@ -1096,7 +1107,7 @@ __device__ __forceinline__ void traceback_pair(const KArgs& a, const PbRun& gA, 
       const PbRun& gp = pb ? gB : gA;
       const int jend_p = pb ? jB : jA;
       const int seg_p = seg;
-      const int top = jend_p / seg_p;
+      const int top = min(T - 1, jend_p / seg_p);
       const int base = 0;  // lane of segment 0
       const int c = pb;    // chain of this PB in every lane
       int exact = __shfl_sync(gmask, c ? psi[1] : psi[0], base + top, T);
