@@ -65,3 +65,22 @@ def test_weak_signal_k7_every_thread_count(ebn0):
         got = gpu_bits(dec, f.llr, f.n_stages, threads_per_pair=T, survivors_in_smem=0)
         assert np.array_equal(got, want), (ebn0, T)
     dec.close()
+
+
+# Block lengths on both sides of the segment rule's switch (K=7, LAMBDA =
+# 56 records of warm-up): lower segments of (J - LAMBDA) / T records when
+# that is at least 2 LAMBDA, else the even split J / T, with J = D + L
+# records per block; at two threads per pair the switch lies at J = 272, at
+# four at J = 488.
+@pytest.mark.parametrize("T, D", [(2, 224), (2, 232), (2, 240), (4, 440), (4, 448), (4, 456)])
+def test_segment_rule_switch_k7(T, D):
+    spec = synth.K7_R12
+    L = 42
+    f = synth.make_frame(spec, 24 * D + 13, 0.0, seed=500 + D)
+    want = oracle_bits(spec, f.llr, f.n_stages, D, L)
+    dec = make_decoder(spec, D, L)
+    for smem in (0, 1):
+        got = gpu_bits(dec, f.llr, f.n_stages, threads_per_pair=T, survivors_in_smem=smem)
+        bad = np.flatnonzero(got != want)
+        assert bad.size == 0, (T, D, smem, bad[:8])
+    dec.close()
